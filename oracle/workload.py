@@ -1,0 +1,25 @@
+"""Twin-experiment assembly of a Burgers problem from seeded draws (oracle side).
+
+xb = x_true0 + Gamma^{1/2} xi_b and y_i = O(x_true(t_i)) + sigma_obs xi_o,i, the
+standard synthetic set-up of Sec. 5.1 (background = truth + prior-distributed
+error, observations = observed truth + observation error).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import burgers, fourdvar, prior
+
+
+def burgers_problem(wl, draws):
+    model = burgers.Burgers1D(wl.n, wl.nu)
+    sym = prior.se_sqrt_symbol(wl.n, wl.sigma_b, wl.length_b)
+    psq = lambda X: prior.apply_symbol(sym, X)
+    prob = fourdvar.FourDVar(model, wl.dt, wl.n_steps, wl.obs_steps, draws["obs_idx"],
+                             wl.sigma_obs, psq)
+    truth = prob.forward(draws["x_true0"])
+    prob.x_true_traj = truth
+    prob.y = prob.observe(truth) + wl.sigma_obs * draws["xi_o"]
+    prob.xb = draws["x_true0"] + psq(draws["xi_b"])
+    prob.symbol = sym
+    return prob

@@ -1,0 +1,188 @@
+"""Seeded synthetic workloads for the SC-4DVAR Gauss-Newton hot path.
+
+This module only *draws* inputs and states workload shapes. It performs none of
+the method's arithmetic: no model step, no prior square root, no observation of a
+trajectory, no solver. The CPU oracle (``oracle/``) and the CUDA library both take
+their inputs from here, so that a parity test feeds both sides the same numbers.
+
+What is drawn here (all with numpy's PCG64 ``default_rng`` from a fixed seed):
+
+* the raw truth field of the 1D Burgers workloads (a sine plus a Gaussian-smoothed
+  white-noise field, Sec. 5.1 uses a sine for the truth; the smoothing recipe is
+  the workload's own),
+* the standard-normal vectors that become the background error (xi_b) and the
+  observation error (xi_o) once a caller applies the prior square root and the
+  observation noise level,
+* observation site indices,
+* dense Gaussian test matrices for tests that pass Omega/Psi explicitly.
+
+The random matrices that the method itself draws inside a Gauss-Newton run
+(Omega, Psi, the kappa test vectors) are NOT drawn here: each side implements the
+Philox4x32-10 counter-based generator from its published definition instead.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+DEFAULT_SEED = 20240128
+
+# Stream offsets for the seeded draws (added to the workload seed).
+STREAM_TRUTH = 0
+STREAM_BACKGROUND = 1
+STREAM_OBS_NOISE = 2
+STREAM_OBS_SITES = 3
+# Stream ids used by the method's own Philox draws (passed to both sides).
+STREAM_SKETCH_BASE = 100
+STREAM_KAPPA_BASE = 200
+STREAM_PSI_OFFSET = 1000
+
+
+@dataclasses.dataclass(frozen=True)
+class BurgersWorkload:
+    """Shape of a periodic 1D viscous Burgers assimilation window.
+
+    ``dt_out`` is the model output step of the workload description; the RK4
+    step is ``dt_out / substeps`` (see :func:`burgers_substeps`).
+    Observations are taken every ``obs_every`` output steps (t0 excluded) at the
+    grid points j with j % obs_stride == 0.
+    """
+    name: str
+    n: int
+    nu: float
+    dt_out: float
+    n_out: int
+    obs_every: int
+    obs_stride: int
+    sigma_obs: float
+    sigma_b: float = 0.1
+    length_b: float = 0.05
+    k: int = 20
+    gn_iters: int = 3
+    pcg_tol: float = 1e-6
+    seed: int = DEFAULT_SEED
+    substeps_override: int | None = None
+
+    @property
+    def dx(self) -> float:
+        return 1.0 / self.n
+
+    @property
+    def substeps(self) -> int:
+        if self.substeps_override is not None:
+            return self.substeps_override
+        return burgers_substeps(self.n, self.nu, self.dt_out)
+
+    @property
+    def dt(self) -> float:
+        return self.dt_out / self.substeps
+
+    @property
+    def n_steps(self) -> int:
+        return self.n_out * self.substeps
+
+    @property
+    def obs_steps(self) -> np.ndarray:
+        """RK step index of every observation time (1-based, t0 excluded)."""
+        t = np.arange(self.obs_every, self.n_out + 1, self.obs_every, dtype=np.int64)
+        return (t * self.substeps).astype(np.int32)
+
+    @property
+    def n_obs_times(self) -> int:
+        return len(self.obs_steps)
+
+    @property
+    def n_obs(self) -> int:
+        return len(range(0, self.n, self.obs_stride))
+
+    @property
+    def m(self) -> int:
+        return self.n_obs_times * self.n_obs
+
+
+def burgers_substeps(n: int, nu: float, dt_out: float, limit: float = 0.6) -> int:
+    """Smallest power of two s with nu*(dt_out/s)/dx^2 <= limit (explicit RK4
+    diffusive stability; the workload's output step is kept as the
+    observation clock)."""
+    dx = 1.0 / n
+    s = 1
+    while nu * (dt_out / s) / (dx * dx) > limit:
+        s *= 2
+    return s
+
+
+BURGERS_WORKLOADS = {
+    # Plain FP64 method, small.
+    "burgers_n128": BurgersWorkload(
+        name="burgers_n128", n=128, nu=0.01, dt_out=1e-3, n_out=50, obs_every=5,
+        obs_stride=4, sigma_obs=0.05, k=20, gn_iters=3),
+    # Burgers at scale (block of k=128 sketch vectors).
+    "burgers_n8192": BurgersWorkload(
+        name="burgers_n8192", n=8192, nu=0.005, dt_out=5e-5, n_out=400, obs_every=10,
+        obs_stride=8, sigma_obs=0.05, k=128, gn_iters=3),
+}
+
+
+def burgers_workload(name: str, **overrides) -> BurgersWorkload:
+    base = BURGERS_WORKLOADS[name]
+    return dataclasses.replace(base, **overrides) if overrides else base
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.default_rng([seed, stream])
+
+
+def periodic_gaussian_weights(n: int, width: float) -> np.ndarray:
+    """Unit-sum periodic Gaussian weights of standard deviation ``width`` on the
+    grid x_j = j/n (used only to smooth the raw truth noise)."""
+    j = np.arange(n)
+    d = np.minimum(j, n - j) / n
+    w = np.exp(-0.5 * (d / width) ** 2)
+    return w / w.sum()
+
+
+def burgers_truth(wl: BurgersWorkload) -> np.ndarray:
+    """x_true(t0) = sin(2 pi x) + G * (0.1 xi), G the unit-sum periodic Gaussian
+    of width 0.05 (a circular convolution, evaluated with numpy.fft)."""
+    n = wl.n
+    x = np.arange(n) / n
+    xi = 0.1 * _rng(wl.seed, STREAM_TRUTH).standard_normal(n)
+    w = periodic_gaussian_weights(n, 0.05)
+    # circular convolution via FFT of two real sequences (input smoothing only)
+    smooth = np.real(np.fft.ifft(np.fft.fft(w) * np.fft.fft(xi)))
+    return np.sin(2.0 * np.pi * x) + smooth
+
+
+def burgers_obs_idx(wl: BurgersWorkload) -> np.ndarray:
+    """Observation sites, shape (n_t, n_o): every obs_stride-th point at every time."""
+    sites = np.arange(0, wl.n, wl.obs_stride, dtype=np.int32)
+    return np.tile(sites, (wl.n_obs_times, 1))
+
+
+def burgers_draws(wl: BurgersWorkload) -> dict:
+    """All seeded random inputs of one Burgers workload."""
+    return {
+        "x_true0": burgers_truth(wl),
+        "xi_b": _rng(wl.seed, STREAM_BACKGROUND).standard_normal(wl.n),
+        "xi_o": _rng(wl.seed, STREAM_OBS_NOISE).standard_normal((wl.n_obs_times, wl.n_obs)),
+        "obs_idx": burgers_obs_idx(wl),
+    }
+
+
+def gaussian_matrix(seed: int, rows: int, cols: int, stream: int = 7) -> np.ndarray:
+    """Dense standard-normal test matrix (column-major use; float64)."""
+    return _rng(seed, stream).standard_normal((rows, cols))
+
+
+def se_prior_params(wl: BurgersWorkload) -> dict:
+    return {"sigma_b": wl.sigma_b, "length": wl.length_b}
+
+
+def describe(wl: BurgersWorkload) -> dict:
+    return {
+        "workload": wl.name, "n": wl.n, "nu": wl.nu, "dt_out": wl.dt_out,
+        "substeps": wl.substeps, "rk_steps": wl.n_steps, "n_t": wl.n_obs_times,
+        "n_o": wl.n_obs, "m": wl.m, "k": wl.k,
+    }
+
