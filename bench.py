@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the SC-4DVAR Gauss-Newton hot path on GB300.
+
+Metric: GN Hessian-vector products per second for a block of k = 128 directions
+(the sketch block of the randomized preconditioners), and the GN-step time to a
+1e-6 relative residual of the sketched mixed-precision solve against plain FP64
+CG (the paper's Prec_Gamma), both on one GB300.
+
+Workload: periodic 1D viscous Burgers, n = 8192, nu = 0.005, output step 5e-5
+over 400 output steps (32 RK4 substeps each, 12 800 RK4 steps), observations
+every 10 output steps at every 8th grid point (m = 40 960), squared-exponential
+prior (sigma_b = 0.1, L = 0.05), synthetic seeded truth / background /
+observations. TLM/ADJ sweeps in FP32, reductions and Gram matrices in FP64.
+
+One timed step = one call of sc4dvar_gn_hessian_apply_block with k = 128 FP32
+directions (prior square root, TLM sweep, ADJ sweep, prior square root, + X).
+The L2 cache (129 MB) is flushed by a 256 MiB write before every timed step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("GN Hessian-vector products/s (block k) and GN-step time to 1e-6 rel. residual "
+          "vs plain FP64 PCG")
+WORKLOAD = "burgers_n8192"
+K_BLOCK = 128
+FP32_PEAK_ALU = 152 * 128 * 2 * 2.070e9   # FMA lanes x 2 flops x max SM clock (flop/s)
+# Algorithmic FP32 flops per grid point per RK4 step of one direction, counted
+# from the tangent-linear / adjoint formulas of the sweeps (base-state stage
+# recomputation not counted): TLM 52, ADJ 55.
+FLOPS_TLM = 52
+FLOPS_ADJ = 55
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-gn-step", action="store_true", help="skip the time-to-solution part")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.lines = []
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def oracle_sample(k_sample=8, n_out=40):
+    """Oracle block Hessian product on a bounded sample of the workload: the full
+    grid and step size, the first n_out output steps (of 400), k_sample directions.
+    Returns (seconds, HVP/s scaled to the full 400-step window, description)."""
+    import sc4dvar_inputs as si
+    from oracle import workload
+    wl_full = si.burgers_workload(WORKLOAD)
+    wl = si.burgers_workload(WORKLOAD, n_out=n_out)
+    draws = si.burgers_draws(wl)
+    ref = workload.burgers_problem(wl, draws)
+    ref.set_iterate(np.zeros(wl.n))
+    X = si.gaussian_matrix(wl.seed, wl.n, k_sample, stream=31)
+    t0 = time.perf_counter()
+    ref.hvp(X)
+    dt = time.perf_counter() - t0
+    scale = wl_full.n_steps / wl.n_steps
+    desc = (f"oracle (numpy FP64, 1 thread) (I+H)X on n={wl.n}, k={k_sample}, first "
+            f"{wl.n_steps} of {wl_full.n_steps} RK4 steps; HVP/s scaled by {scale:g} to the full window")
+    return dt, k_sample / (dt * scale), desc
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import sc4dvar_inputs as si
+    wl = si.burgers_workload(WORKLOAD)
+    times, vals = [], []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        dt, v, desc = oracle_sample(k_sample=4, n_out=20)
+        if i >= args.warmup:
+            times.append(dt)
+            vals.append(v)
+    value = statistics.mean(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "HVP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(wl),
+        "cpu_baseline": {"value": value, "unit": "HVP/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "HVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def config_dict(wl):
+    return {"workload": f"{wl.name}: periodic Burgers n={wl.n}, nu={wl.nu}, {wl.n_steps} RK4 steps "
+                        f"(dt_out={wl.dt_out}, {wl.substeps} substeps), m={wl.m} observations, "
+                        f"block k={K_BLOCK}, FP32 sweeps",
+            "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": K_BLOCK,
+            "l2": "256 MiB write before every timed step"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def setup_problem(torch, dev):
+    import paper_2401_15758_gb300 as g
+    import sc4dvar_inputs as si
+    wl = si.burgers_workload(WORKLOAD)
+    d = si.burgers_draws(wl)
+    prob = g.Problem.from_workload(wl, d["obs_idx"])
+    xt = torch.tensor(d["x_true0"], device=dev)
+    obs, _ = prob.forecast(xt)
+    y = obs + wl.sigma_obs * torch.tensor(d["xi_o"].reshape(-1), device=dev)
+    xb = xt + prob.prior_sqrt_apply(torch.tensor(d["xi_b"], device=dev))
+    prob.set_background(xb)
+    prob.set_observations(y)
+    v0 = torch.zeros(wl.n, dtype=torch.float64, device=dev)
+    J0 = prob.fwd(v0)
+    return g, si, wl, prob, J0
+
+
+def gpu_arm(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    g, si, wl, prob, J0 = setup_problem(torch, dev)
+    stream = torch.cuda.current_stream()
+    k = K_BLOCK
+    X = torch.tensor(si.gaussian_matrix(wl.seed, k, wl.n, stream=21), device=dev, dtype=torch.float32)
+    Y = torch.empty_like(X)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        prob.gn_hessian_apply_block(X, prec=g.FP32, out=Y)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = g.lib.sc4dvar_launch_count()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = g.lib.sc4dvar_launch_count() - l0
+    if dist:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    hvps = k * args.steps * world
+    value = hvps / (total_ms / 1e3)
+
+    # dominant kernels: ADJ and TLM sweeps timed alone (each call = sweep + one prior FFT pass)
+    W = torch.empty((k, wl.m), dtype=torch.float32, device=dev)
+    Z = torch.empty_like(X)
+    kern = {}
+    for name, fn in (("tlm", lambda: prob.tlm_block(X, prec=g.FP32, out=W)),
+                     ("adj", lambda: prob.adj_block(W, prec=g.FP32, out=Z))):
+        fn()
+        reps = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            reps.append(a.elapsed_time(b))
+        kern[name] = statistics.mean(reps)
+    clk = clocks.stop()
+    dom = max(kern, key=kern.get)
+    flops = (FLOPS_ADJ if dom == "adj" else FLOPS_TLM) * wl.n * wl.n_steps * k
+    achieved = flops / (kern[dom] / 1e3) / 1e12
+    peak = FP32_PEAK_ALU / 1e12
+    roofline = {"bound": "alu", "kernel": f"burgers_{dom}_kernel<float>", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (unit counts)",
+                "kernel_ms": kern}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Xh = X.cpu().pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
+    Xd = torch.empty_like(X)
+    Yd = torch.empty_like(X)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Xd.copy_(Xh, non_blocking=True)
+        prob.gn_hessian_apply_block(Xd, prec=g.FP32, out=Yd)
+        Yh.copy_(Yd, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_val = k * world / (statistics.mean(e2e_ms) / 1e3)
+    e2e = {"value": e2e_val, "unit": "HVP/s", "h2d_bytes_per_step": Xh.numel() * 4,
+           "d2h_bytes_per_step": Yh.numel() * 4}
+
+    gn = None
+    if not args.no_gn_step:
+        gn = gn_step(torch, g, prob, wl, dev)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "HVP/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": config_dict(wl), "roofline": roofline,
+               "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+        if gn is not None:
+            out["gn_step"] = gn
+        if not args.no_cpu_baseline:
+            dt, v, desc = oracle_sample()
+            out["cpu_baseline"] = {"value": v, "unit": "HVP/s", "cores": 1, "kind": "oracle",
+                                   "sample": desc, "seconds": dt}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def gn_step(torch, g, prob, wl, dev):
+    """GN-step time to a 1e-6 relative residual at the background iterate:
+    sketched (RandSVD, k=128, FP32 sweeps) PCG with FP64 defect correction vs
+    plain FP64 CG (Prec_Gamma). FWD and gradient are shared by both and timed apart."""
+    v0 = torch.zeros(wl.n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prob.fwd(v0)
+    gv = prob.gradient()
+    torch.cuda.synchronize()
+    t_fg = time.perf_counter() - t0
+    b = -gv
+    res = {}
+    # method
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pc = prob.build_precond("randsvd", l=K_BLOCK, prec=g.FP32, seed=wl.seed)
+    torch.cuda.synchronize()
+    t_sk = time.perf_counter() - t0
+    x, info = prob.pcg(b, pc, tol=1e-6, prec=g.FP32, refine=3)
+    torch.cuda.synchronize()
+    t_m = time.perf_counter() - t0
+    res["method"] = {"seconds": t_m, "sketch_seconds": t_sk, "pcg_its": info["iterations"],
+                     "restarts": info["restarts"], "relres_fp64": info["relres"],
+                     "status": info["status"], "rank": pc.rank}
+    # plain FP64 CG
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xp, infop = prob.pcg(b, None, tol=1e-6, prec=g.FP64)
+    torch.cuda.synchronize()
+    t_p = time.perf_counter() - t0
+    # true FP64 residuals of both solutions (outside the timed regions)
+    def true_rel(xx):
+        r = b - prob.gn_hessian_apply_block(xx.reshape(1, -1)).reshape(-1)
+        return float(torch.linalg.norm(r) / torch.linalg.norm(b))
+    res["plain_fp64_cg"] = {"seconds": t_p, "pcg_its": infop["iterations"],
+                            "relres_fp64": true_rel(xp), "status": infop["status"]}
+    res["method"]["relres_fp64_check"] = true_rel(x)
+    res["step_diff"] = float(torch.linalg.norm(x - xp) / torch.linalg.norm(xp))
+    res["speedup"] = t_p / t_m
+    res["fwd_gradient_seconds"] = t_fg
+    res["unit"] = "s"
+    pc.close()
+    return res
+
+
+def profile_case():
+    """One FP32 TLM block and one FP32 ADJ block (k = 128) on the first 40 output
+    steps of the workload (1280 RK4 steps): the kernels of the timed step on a
+    window short enough for an ncu capture."""
+    import torch
+    import paper_2401_15758_gb300 as g
+    import sc4dvar_inputs as si
+    wl = si.burgers_workload(WORKLOAD, n_out=40)
+    d = si.burgers_draws(wl)
+    prob = g.Problem.from_workload(wl, d["obs_idx"])
+    prob.set_background(torch.tensor(d["x_true0"], device="cuda"))
+    prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
+    X = torch.tensor(si.gaussian_matrix(wl.seed, K_BLOCK, wl.n, stream=21), device="cuda",
+                     dtype=torch.float32)
+    W = prob.tlm_block(X, prec=g.FP32)
+    prob.adj_block(W, prec=g.FP32)
+    torch.cuda.synchronize()
+    print("profile case done")
+
+
+def main():
+    args = parse()
+    if args.profile:
+        profile_case()
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,269 @@
+/*
+ * sc4dvar.h -- C ABI of the GB300 SC-4DVAR Gauss-Newton library.
+ *
+ * The library implements the hot path of the strong-constraint 4D-Var
+ * Gauss-Newton solve of Cheng, Rao, Sandu and Saibaba, "Randomized
+ * preconditioned solvers for strong constraint 4D-Var data assimilation"
+ * (arXiv 2401.15758): block Gauss-Newton Hessian products through tangent-linear
+ * (TLM) and adjoint (ADJ) sweeps of a discretized model, the randomized low-rank
+ * preconditioners built from them (RandSVD, Nystrom, SingleView; fixed or
+ * adaptive size; reuse or recompute), and the preconditioned CG that uses them.
+ *
+ * Conventions (every entry point):
+ *  - Return value: SC4DVAR_OK (0) or a negative SC4DVAR_ERR_* code. Nothing
+ *    throws across the ABI. sc4dvar_last_error() returns a message for the last
+ *    failing call on the calling thread.
+ *  - Pointers named *_dev are device pointers owned by the caller; the library
+ *    never frees them. Pointers named *_host are host pointers.
+ *  - Dense blocks are column-major with an explicit leading dimension (ld >= rows).
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Calls are asynchronous on that stream unless the description says
+ *    that they return a host value; those synchronize the stream.
+ *  - prec selects the arithmetic of the TLM/ADJ sweeps and the element type of
+ *    the block buffers: SC4DVAR_FP64 -> double*, SC4DVAR_FP32 -> float*.
+ *    Vectors of the outer iteration (v, g, d, PCG vectors) are always double.
+ *  - Opaque handles own device workspaces (the stored trajectory, sketches) and
+ *    are released with the matching *_destroy call.
+ *
+ * The control variable: x0 = xb + Gamma^{1/2} v. In v the GN system of
+ * Eq. (gniterf1)/(pcgsystem) reads (I + H) dv = -g_v with H = A^T A and
+ *   A = [ R_i^{-1/2} O_i M_i Gamma^{1/2} ]_{i=1..n_t}    (Eq. Rhalf, m x n),
+ * rows ordered time-major (row i*n_o + o).
+ */
+#ifndef SC4DVAR_H
+#define SC4DVAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define SC4DVAR_OK                 0
+#define SC4DVAR_ERR_INVALID_ARG   -1
+#define SC4DVAR_ERR_CUDA          -2
+#define SC4DVAR_ERR_NOT_SPD       -3   /* a Cholesky factorization failed        */
+#define SC4DVAR_ERR_BREAKDOWN     -4   /* PCG: p^T (I+H) p <= 0 or not finite     */
+#define SC4DVAR_ERR_NOT_CONVERGED -5   /* PCG: maxit reached above tolerance      */
+#define SC4DVAR_ERR_TIMEOUT       -6   /* a bounded device wait gave up           */
+#define SC4DVAR_ERR_OOM           -7
+#define SC4DVAR_ERR_STATE         -8   /* e.g. no forward trajectory stored yet   */
+
+/* ---- enumerations ------------------------------------------------------- */
+#define SC4DVAR_MODEL_BURGERS1D 1      /* periodic 1D viscous Burgers, Sec. 5.1  */
+#define SC4DVAR_MODEL_BVE2D     2      /* doubly periodic barotropic vorticity   */
+
+#define SC4DVAR_FP64 0
+#define SC4DVAR_FP32 1
+
+#define SC4DVAR_PRIOR_SYMBOL    0      /* caller gives the Fourier symbol of Gamma^{1/2} */
+#define SC4DVAR_PRIOR_SE        1      /* sigma_b^2 exp(-d^2/(2 L^2)), periodic distance */
+
+#define SC4DVAR_SKETCH_NONE       0    /* Prec_Gamma: plain CG on (I + H)           */
+#define SC4DVAR_SKETCH_RANDSVD    1    /* Alg. 1 (adaptive: Alg. 4)                 */
+#define SC4DVAR_SKETCH_NYSTROM    2    /* Alg. 2 (adaptive: grown sketch, Alg. 2)   */
+#define SC4DVAR_SKETCH_SINGLEVIEW 3    /* Alg. 3 (adaptive: Alg. 5)                 */
+
+/* Philox stream ids of the method's own random draws at GN iteration k
+ * (seed = sc4dvar_sketch_opts.seed / sc4dvar_gn_opts.seed):
+ *   Omega  <- stream SC4DVAR_STREAM_SKETCH + k
+ *   Psi    <- stream SC4DVAR_STREAM_SKETCH + k + SC4DVAR_STREAM_PSI
+ *   kappa  <- stream SC4DVAR_STREAM_KAPPA + k (column 0: kappa_re, 1.. kappa_sk)
+ * Element (i, j) of a rows x cols draw is the Box-Muller normal number
+ * e = i + rows * j of that stream (Philox4x32-10, counter (e/2, stream), key seed). */
+#define SC4DVAR_STREAM_SKETCH 100
+#define SC4DVAR_STREAM_KAPPA  200
+#define SC4DVAR_STREAM_PSI    1000
+
+typedef struct sc4dvar_problem_s* sc4dvar_problem_t;
+typedef struct sc4dvar_precond_s* sc4dvar_precond_t;
+
+/* Problem description (all pointers are host pointers, copied at creation). */
+typedef struct {
+    int model;             /* SC4DVAR_MODEL_*                                        */
+    int nx, ny;            /* grid; Burgers: n = nx (power of two, 8..16384), ny = 1 */
+    double nu;             /* viscosity                                              */
+    double dt;             /* RK4 step                                               */
+    int n_steps;           /* RK4 steps in the window (N)                            */
+    int n_obs_times;       /* n_t                                                    */
+    const int* obs_steps;  /* [n_t] RK step of each observation time, 1..N, increasing */
+    int n_obs;             /* n_o sites per observation time                         */
+    const int* obs_idx;    /* [n_t * n_o] grid indices (time-major)                  */
+    double sigma_obs;      /* R_i = sigma_obs^2 I                                    */
+    int prior_kind;        /* SC4DVAR_PRIOR_*                                        */
+    double prior_sigma;    /* SE: sigma_b                                            */
+    double prior_length;   /* SE: correlation length L                               */
+    const double* prior_symbol; /* SYMBOL: [n] real even Fourier symbol of Gamma^{1/2} */
+    double forcing_amp;    /* BVE forcing amplitude (F = amp sin(k y))                */
+    int forcing_k;         /* BVE forcing wavenumber                                 */
+} sc4dvar_problem_desc;
+
+/* Sketch options (Sec. 3.1). */
+typedef struct {
+    int method;            /* SC4DVAR_SKETCH_*                                   */
+    int l;                 /* l (RandSVD, Nystrom) or l_1 (SingleView); initial size when adaptive */
+    int l2;                /* SingleView l_2; <= 0 selects 2 l_1 + 1             */
+    int adaptive;          /* 1: grow by l_hat until kappa_sk <= eps_sk          */
+    int l_hat;             /* adaptive increment; <= 0 selects l / 2             */
+    int l_max;             /* adaptive cap; <= 0 selects min(8 l, n)             */
+    double eps_sk;         /* adaptive tolerance (Eq. condtext), e.g. 1.01        */
+    uint64_t seed;         /* Philox key                                          */
+    int gn_iter;           /* GN iteration index k (selects the Philox streams)   */
+    int prec;              /* SC4DVAR_FP64 / SC4DVAR_FP32 sweeps and sketch storage */
+} sc4dvar_sketch_opts;
+
+typedef struct {
+    double tol;            /* relative residual |r|/|b| of the recurrence residual  */
+    int maxit;             /* <= 0 selects n                                        */
+    int prec;              /* operator precision of the inner iteration             */
+    int refine;            /* FP32 operator only: max FP64 defect-correction restarts */
+} sc4dvar_pcg_opts;
+
+typedef struct {
+    int iterations;        /* PCG iterations (all restarts)                        */
+    int restarts;          /* defect-correction restarts performed                 */
+    double relres;         /* final |b - (I+H) x| / |b| with the FP64 operator     */
+    int status;            /* SC4DVAR_OK / _BREAKDOWN / _NOT_CONVERGED             */
+} sc4dvar_pcg_info;
+
+typedef struct {
+    int iters;             /* GN iterations                                       */
+    double gtol;           /* stop when |g_k|_inf / |g_0|_inf < gtol (0: never)   */
+    sc4dvar_sketch_opts sketch;   /* method NONE = Prec_Gamma                      */
+    double eps_re;         /* reuse tolerance (Eq. condtext2); adaptive only       */
+    sc4dvar_pcg_opts pcg;
+} sc4dvar_gn_opts;
+
+#define SC4DVAR_GN_MAX_ITERS 64
+typedef struct {
+    int iters_done;
+    double J[SC4DVAR_GN_MAX_ITERS];        /* cost at each iterate                 */
+    double g_inf[SC4DVAR_GN_MAX_ITERS];    /* |g_v|_inf at each iterate            */
+    int pcg_its[SC4DVAR_GN_MAX_ITERS];
+    double relres[SC4DVAR_GN_MAX_ITERS];
+    int sketched[SC4DVAR_GN_MAX_ITERS];    /* 1 if a new sketch was built          */
+    int rank[SC4DVAR_GN_MAX_ITERS];        /* sketch size in use                   */
+    double kappa_re[SC4DVAR_GN_MAX_ITERS]; /* reuse estimate (0 when not computed) */
+} sc4dvar_gn_info;
+
+/* Counters in the paper's accounting (Sec. 5, Tables 3-5): a Hessian product
+ * counts one TLM and one ADJ per column; a sketch counts its TLM/ADJ columns as
+ * offline; kappa estimates are counted apart. */
+typedef struct {
+    int64_t fwd;
+    int64_t tlm_online, adj_online;
+    int64_t tlm_offline, adj_offline;
+    int64_t tlm_kappa, adj_kappa;
+} sc4dvar_counters_t;
+
+/* ---- library --------------------------------------------------------------- */
+const char* sc4dvar_last_error(void);
+int sc4dvar_version(void);
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * threads, all devices). A diagnostic with no counterpart in the paper, used to
+ * count the kernels inside a timed region. */
+long long sc4dvar_launch_count(void);
+
+/* ---- problem ---------------------------------------------------------------
+ * sc4dvar_problem_create: validates the description, copies the observation
+ * pattern to the device, computes the prior symbol and allocates the trajectory
+ * store ((N+1) x n doubles and (N+1) x n floats). Returns ERR_INVALID_ARG for
+ * an unsupported grid, ERR_OOM if allocation fails. Runs on the default stream
+ * and synchronizes it. */
+int sc4dvar_problem_create(const sc4dvar_problem_desc* desc, sc4dvar_problem_t* out);
+int sc4dvar_problem_destroy(sc4dvar_problem_t p);
+/* n (state size) and m (= n_t * n_o) of a problem. */
+int sc4dvar_problem_dims(sc4dvar_problem_t p, int* n, int* m);
+
+/* Background xb [n] and observations y [m] (time-major), device doubles. */
+int sc4dvar_set_background(sc4dvar_problem_t p, const double* xb_dev, void* stream);
+int sc4dvar_set_observations(sc4dvar_problem_t p, const double* y_dev, void* stream);
+
+/* Y = Gamma^{1/2} X for k columns (FP64). The prior square root used by A. */
+int sc4dvar_prior_sqrt_apply(sc4dvar_problem_t p, const double* X_dev, int ldx, int k,
+                             double* Y_dev, int ldy, void* stream);
+/* The prior symbol actually in use (n doubles, host), for inspection. */
+int sc4dvar_prior_symbol(sc4dvar_problem_t p, double* symbol_host);
+
+/* Model run from an arbitrary initial state x0 [n] (FP64): writes O x_{t_i} for
+ * every observation time to obs_dev [m] (time-major) and, if xN_dev is not
+ * NULL, the final state. Does not touch the stored trajectory. */
+int sc4dvar_forecast(sc4dvar_problem_t p, const double* x0_dev, double* obs_dev,
+                     double* xN_dev, void* stream);
+
+/* FWD at the iterate v [n]: x0 = xb + Gamma^{1/2} v, the FP64 trajectory (and
+ * its FP32 copy) is stored in the handle, d = R^{-1/2}(O x_i - y_i) is formed.
+ * Eq. 4dvar_cf: J(v) = 1/2 |v|^2 + 1/2 |d|^2. If J_host is not NULL the call
+ * synchronizes and returns J. d_dev [m] is optional. */
+int sc4dvar_fwd(sc4dvar_problem_t p, const double* v_dev, double* J_host, double* d_dev,
+                void* stream);
+
+/* g_v = v + A^T d at the stored iterate (Eq. 4dvar_gradient, in v); one FP64
+ * ADJ sweep. ERR_STATE if sc4dvar_fwd was not called. */
+int sc4dvar_gradient(sc4dvar_problem_t p, double* g_dev, void* stream);
+
+/* A X (Eq. Rhalf): Gamma^{1/2}, then the TLM sweep of k columns; W is m x k. */
+int sc4dvar_tlm_block(sc4dvar_problem_t p, const void* X_dev, int ldx, int k,
+                      void* W_dev, int ldw, int prec, void* stream);
+/* A^T W (Eq. Rhalf): the ADJ sweep of k columns, then Gamma^{1/2}; X is n x k. */
+int sc4dvar_adj_block(sc4dvar_problem_t p, const void* W_dev, int ldw, int k,
+                      void* X_dev, int ldx, int prec, void* stream);
+/* Y = (I + A^T A) X, or A^T A X when misfit_only != 0 (Eq. Rhalf / gniterf1):
+ * one TLM and one ADJ sweep per column, all k columns at once. Needs internal
+ * scratch for A X (m x k in the problem's workspace, grown on demand). */
+int sc4dvar_gn_hessian_apply_block(sc4dvar_problem_t p, const void* X_dev, int ldx, int k,
+                                   void* Y_dev, int ldy, int misfit_only, int prec,
+                                   void* stream);
+
+/* ---- preconditioners (Sec. 3.1) ---------------------------------------------
+ * Builds H_hat = V diag(lam) V^T at the stored iterate with Alg. 1/2/3 (or their
+ * adaptive forms). Omega_dev (n x l, double, ld n) may be NULL (then drawn with
+ * Philox from opts->seed / gn_iter); Psi_dev likewise (m x l2). Synchronizes.
+ * ERR_NOT_SPD if a Cholesky factorization fails. */
+int sc4dvar_build_precond(sc4dvar_problem_t p, const sc4dvar_sketch_opts* opts,
+                          const double* Omega_dev, const double* Psi_dev,
+                          sc4dvar_precond_t* out, void* stream);
+int sc4dvar_precond_destroy(sc4dvar_precond_t P);
+/* rank l and, optionally, lam [l] (descending) and V (n x l, ld n) copied to host. */
+int sc4dvar_precond_info(sc4dvar_precond_t P, int* rank, double* lam_host, double* V_host);
+/* Z = (I + V Lam V^T)^{-1} R (Eq. woodbury) for k columns, FP64. */
+int sc4dvar_precond_apply(sc4dvar_precond_t P, const double* R_dev, int ldr, int k,
+                          double* Z_dev, int ldz, void* stream);
+/* kappa = |(I + H)(I + H_hat)^{-1} v|_2 with v = w/|w|, w the Philox column
+ * `column` of stream (seed, stream_id) (Eqs. condtext, condtext2); one FP64
+ * Hessian product. P = NULL gives |(I + H) v|. Synchronizes. */
+int sc4dvar_kappa_estimate(sc4dvar_problem_t p, sc4dvar_precond_t P, uint64_t seed,
+                           uint64_t stream_id, int column, double* kappa_host, void* stream);
+
+/* ---- solvers ------------------------------------------------------------------
+ * PCG on (I + H) x = b (Eq. pcgsystem), x0 = 0, preconditioned by P
+ * (NULL = Prec_Gamma). FP64 vectors and reductions; the operator runs in
+ * opts->prec. With FP32 and refine > 0 the iteration is restarted on the FP64
+ * residual b - (I + H) x (defect correction) until that residual meets tol.
+ * Synchronizes; info may be NULL. */
+int sc4dvar_pcg(sc4dvar_problem_t p, sc4dvar_precond_t P, const double* b_dev, double* x_dev,
+                const sc4dvar_pcg_opts* opts, sc4dvar_pcg_info* info, void* stream);
+
+/* SketchSolv step (Eq. dxsol, in v): dv = -(I + H_hat)^{-1} g. */
+int sc4dvar_sketchsolv(sc4dvar_precond_t P, const double* g_dev, double* dv_dev, void* stream);
+
+/* Gauss-Newton from v_inout (overwritten with the final iterate): per iteration
+ * FWD, gradient, sketch (every iteration when fixed; when adaptive, the last
+ * sketch is reused while kappa_re < eps_re, Sec. 3.2), PCG, v += dv.
+ * Synchronizes. info may be NULL. */
+int sc4dvar_gauss_newton(sc4dvar_problem_t p, const sc4dvar_gn_opts* opts, double* v_inout_dev,
+                         sc4dvar_gn_info* info, void* stream);
+
+int sc4dvar_counters(sc4dvar_problem_t p, sc4dvar_counters_t* out);
+int sc4dvar_counters_reset(sc4dvar_problem_t p);
+
+/* Device Gaussian draw (the method's convention above): out (rows x cols, ld
+ * rows, double) = columns col0.. of stream (seed, stream_id). */
+int sc4dvar_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, int64_t col0,
+                     double* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SC4DVAR_H */

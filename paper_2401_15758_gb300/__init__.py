@@ -1,0 +1,270 @@
+"""GB300 SC-4DVAR Gauss-Newton library: thin Python binding of include/sc4dvar.h.
+
+Every numerical step runs in the CUDA kernels of libsc4dvar.so; this module only
+turns torch tensors (device memory, streams) into pointers and sizes. Importing
+it loads the library and raises if the library cannot be built or loaded: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import (FP32, FP64, MODEL_BURGERS1D, PRIOR_SE, PRIOR_SYMBOL, SKETCH_NONE,  # noqa: F401
+                   SKETCH_NYSTROM, SKETCH_RANDSVD, SKETCH_SINGLEVIEW, STREAM_KAPPA, STREAM_PSI,
+                   STREAM_SKETCH, Sc4dvarError)
+
+lib = _abi.load()
+check = _abi.check
+
+METHODS = {"none": SKETCH_NONE, "randsvd": SKETCH_RANDSVD, "nystrom": SKETCH_NYSTROM,
+           "singleview": SKETCH_SINGLEVIEW}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype(prec):
+    torch = _torch()
+    return torch.float64 if prec == FP64 else torch.float32
+
+
+class Precond:
+    """Low-rank H_hat = V diag(lam) V^T (Sec. 3.1); owns its device arrays."""
+
+    def __init__(self, handle, n):
+        self.h = handle
+        self.n = n
+
+    @property
+    def rank(self):
+        r = C.c_int()
+        check(lib.sc4dvar_precond_info(self.h, C.byref(r), None, None))
+        return r.value
+
+    def arrays(self):
+        r = self.rank
+        lam = np.zeros(max(r, 1))
+        V = np.zeros((max(r, 1), self.n))
+        check(lib.sc4dvar_precond_info(self.h, None, lam.ctypes.data_as(C.c_void_p),
+                                       V.ctypes.data_as(C.c_void_p)))
+        return V[:r].T.copy(), lam[:r].copy()
+
+    def apply(self, R, stream=None):
+        """(I + H_hat)^{-1} R (Eq. woodbury); R is (n,) or (k, n) float64."""
+        R2 = R.reshape(-1, self.n).contiguous()
+        Z = _torch().empty_like(R2)
+        check(lib.sc4dvar_precond_apply(self.h, _ptr(R2), self.n, R2.shape[0], _ptr(Z), self.n,
+                                        _stream(stream)))
+        return Z.reshape(R.shape)
+
+    def sketchsolv(self, g, stream=None):
+        """dv = -(I + H_hat)^{-1} g (Eq. dxsol in the control variable)."""
+        dv = _torch().empty_like(g)
+        check(lib.sc4dvar_sketchsolv(self.h, _ptr(g), _ptr(dv), _stream(stream)))
+        return dv
+
+    def close(self):
+        if self.h:
+            lib.sc4dvar_precond_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Problem:
+    """One SC-4DVAR assimilation window (handle of sc4dvar_problem_create).
+
+    Blocks are torch tensors of shape (k, n) / (k, m) whose rows are the columns
+    of the column-major C blocks (so a contiguous (k, n) tensor is an n x k block
+    with leading dimension n).
+    """
+
+    def __init__(self, *, n, nu, dt, n_steps, obs_steps, obs_idx, sigma_obs,
+                 prior_sigma=None, prior_length=None, prior_symbol=None):
+        obs_steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
+        obs_idx = np.ascontiguousarray(obs_idx, dtype=np.int32)
+        d = _abi.ProblemDesc()
+        d.model = MODEL_BURGERS1D
+        d.nx, d.ny = int(n), 1
+        d.nu, d.dt, d.n_steps = float(nu), float(dt), int(n_steps)
+        d.n_obs_times = int(obs_idx.shape[0])
+        d.n_obs = int(obs_idx.shape[1])
+        d.obs_steps = obs_steps.ctypes.data_as(C.POINTER(C.c_int))
+        d.obs_idx = obs_idx.ctypes.data_as(C.POINTER(C.c_int))
+        d.sigma_obs = float(sigma_obs)
+        if prior_symbol is not None:
+            sym = np.ascontiguousarray(prior_symbol, dtype=np.float64)
+            d.prior_kind = PRIOR_SYMBOL
+            d.prior_symbol = sym.ctypes.data_as(C.POINTER(C.c_double))
+        else:
+            d.prior_kind = PRIOR_SE
+            d.prior_sigma, d.prior_length = float(prior_sigma), float(prior_length)
+        h = C.c_void_p()
+        check(lib.sc4dvar_problem_create(C.byref(d), C.byref(h)))
+        self.h = h
+        nn, mm = C.c_int(), C.c_int()
+        check(lib.sc4dvar_problem_dims(h, C.byref(nn), C.byref(mm)))
+        self.n, self.m = nn.value, mm.value
+
+    @classmethod
+    def from_workload(cls, wl, obs_idx, **kw):
+        return cls(n=wl.n, nu=wl.nu, dt=wl.dt, n_steps=wl.n_steps, obs_steps=wl.obs_steps,
+                   obs_idx=obs_idx, sigma_obs=wl.sigma_obs, prior_sigma=wl.sigma_b,
+                   prior_length=wl.length_b, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.sc4dvar_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- data -----------------------------------------------------------------
+    def set_background(self, xb, stream=None):
+        check(lib.sc4dvar_set_background(self.h, _ptr(xb), _stream(stream)))
+
+    def set_observations(self, y, stream=None):
+        check(lib.sc4dvar_set_observations(self.h, _ptr(y), _stream(stream)))
+
+    def prior_symbol(self):
+        s = np.zeros(self.n)
+        check(lib.sc4dvar_prior_symbol(self.h, s.ctypes.data_as(C.c_void_p)))
+        return s
+
+    def prior_sqrt_apply(self, X, stream=None):
+        """Gamma^{1/2} X for X of shape (n,) or (k, n), float64."""
+        X2 = X.reshape(-1, self.n).contiguous()
+        Y = _torch().empty_like(X2)
+        check(lib.sc4dvar_prior_sqrt_apply(self.h, _ptr(X2), self.n, X2.shape[0], _ptr(Y), self.n,
+                                           _stream(stream)))
+        return Y.reshape(X.shape)
+
+    def forecast(self, x0, stream=None):
+        """O x_{t_i} for all observation times (m,), and the final state (n,)."""
+        torch = _torch()
+        obs = torch.empty(self.m, dtype=torch.float64, device=x0.device)
+        xN = torch.empty(self.n, dtype=torch.float64, device=x0.device)
+        check(lib.sc4dvar_forecast(self.h, _ptr(x0), _ptr(obs), _ptr(xN), _stream(stream)))
+        return obs, xN
+
+    # -- the path ---------------------------------------------------------------
+    def fwd(self, v, want_d=False, stream=None):
+        """x0 = xb + Gamma^{1/2} v, FWD sweep; returns J(v) (and d if asked)."""
+        J = C.c_double()
+        d = _torch().empty(self.m, dtype=_torch().float64, device=v.device) if want_d else None
+        check(lib.sc4dvar_fwd(self.h, _ptr(v), C.byref(J), _ptr(d), _stream(stream)))
+        return (J.value, d) if want_d else J.value
+
+    def gradient(self, stream=None, out=None):
+        g = out if out is not None else _torch().empty(self.n, dtype=_torch().float64, device="cuda")
+        check(lib.sc4dvar_gradient(self.h, _ptr(g), _stream(stream)))
+        return g
+
+    def tlm_block(self, X, prec=FP64, stream=None, out=None):
+        """A X (Eq. Rhalf). X: (k, n) -> (k, m)."""
+        X2 = X.reshape(-1, self.n).contiguous()
+        k = X2.shape[0]
+        W = out if out is not None else _torch().empty((k, self.m), dtype=_dtype(prec), device=X.device)
+        check(lib.sc4dvar_tlm_block(self.h, _ptr(X2), self.n, k, _ptr(W), self.m, prec, _stream(stream)))
+        return W
+
+    def adj_block(self, W, prec=FP64, stream=None, out=None):
+        """A^T W (Eq. Rhalf). W: (k, m) -> (k, n)."""
+        W2 = W.reshape(-1, self.m).contiguous()
+        k = W2.shape[0]
+        X = out if out is not None else _torch().empty((k, self.n), dtype=_dtype(prec), device=W.device)
+        check(lib.sc4dvar_adj_block(self.h, _ptr(W2), self.m, k, _ptr(X), self.n, prec, _stream(stream)))
+        return X
+
+    def gn_hessian_apply_block(self, X, misfit_only=False, prec=FP64, stream=None, out=None):
+        """(I + A^T A) X, or A^T A X. X: (k, n) -> (k, n)."""
+        X2 = X.reshape(-1, self.n).contiguous()
+        k = X2.shape[0]
+        Y = out if out is not None else _torch().empty_like(X2)
+        check(lib.sc4dvar_gn_hessian_apply_block(self.h, _ptr(X2), self.n, k, _ptr(Y), self.n,
+                                                 int(misfit_only), prec, _stream(stream)))
+        return Y.reshape(X.shape) if out is None else Y
+
+    def build_precond(self, method="randsvd", l=20, l2=0, adaptive=False, l_hat=0, l_max=0,
+                      eps_sk=1.01, seed=20240128, gn_iter=0, prec=FP64, Omega=None, Psi=None,
+                      stream=None):
+        """Sketch H at the stored iterate (Algs. 1-5). Omega: (l, n) float64 rows = columns."""
+        o = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed,
+                            gn_iter, prec)
+        h = C.c_void_p()
+        Om = None if Omega is None else Omega.contiguous()
+        Ps = None if Psi is None else Psi.contiguous()
+        check(lib.sc4dvar_build_precond(self.h, C.byref(o), _ptr(Om), _ptr(Ps), C.byref(h),
+                                        _stream(stream)))
+        return Precond(h, self.n)
+
+    def kappa_estimate(self, precond=None, seed=20240128, stream_id=STREAM_KAPPA, column=0,
+                       stream=None):
+        k = C.c_double()
+        check(lib.sc4dvar_kappa_estimate(self.h, None if precond is None else precond.h, seed,
+                                         stream_id, column, C.byref(k), _stream(stream)))
+        return k.value
+
+    def pcg(self, b, precond=None, tol=1e-6, maxit=0, prec=FP64, refine=2, stream=None, x=None):
+        x = _torch().empty_like(b) if x is None else x
+        o = _abi.PcgOpts(tol, maxit, prec, refine)
+        info = _abi.PcgInfo()
+        check(lib.sc4dvar_pcg(self.h, None if precond is None else precond.h, _ptr(b), _ptr(x),
+                              C.byref(o), C.byref(info), _stream(stream)))
+        return x, {"iterations": info.iterations, "restarts": info.restarts,
+                   "relres": info.relres, "status": info.status}
+
+    def gauss_newton(self, v, iters=3, method="none", l=20, adaptive=False, l2=0, l_hat=0,
+                     l_max=0, eps_sk=1.01, eps_re=10.0, tol=1e-6, maxit=0, prec=FP64, refine=2,
+                     gtol=0.0, seed=20240128, stream=None):
+        """Gauss-Newton in place on v (float64, (n,)); returns the per-iteration record."""
+        so = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed, 0, prec)
+        o = _abi.GnOpts(iters, gtol, so, eps_re, _abi.PcgOpts(tol, maxit, prec, refine))
+        info = _abi.GnInfo()
+        check(lib.sc4dvar_gauss_newton(self.h, C.byref(o), _ptr(v), C.byref(info), _stream(stream)))
+        k = info.iters_done
+        return [{"J": info.J[i], "g_inf": info.g_inf[i], "pcg_its": info.pcg_its[i],
+                 "relres": info.relres[i], "sketched": bool(info.sketched[i]),
+                 "rank": info.rank[i], "kappa_re": info.kappa_re[i]} for i in range(k)]
+
+    def counters(self):
+        c = _abi.Counters()
+        check(lib.sc4dvar_counters(self.h, C.byref(c)))
+        return {f: getattr(c, f) for f, _ in _abi.Counters._fields_}
+
+    def counters_reset(self):
+        check(lib.sc4dvar_counters_reset(self.h))
+
+
+def gaussian(seed, stream_id, rows, cols, col0=0, stream=None):
+    """(cols, rows) float64 tensor: columns col0.. of the method's Philox stream."""
+    torch = _torch()
+    out = torch.empty((cols, rows), dtype=torch.float64, device="cuda")
+    check(lib.sc4dvar_gaussian(seed, stream_id, rows, cols, col0, _ptr(out), _stream(stream)))
+    return out

@@ -1,0 +1,1223 @@
+// C ABI of the sc4dvar library: problem handles, the model operators of
+// Eq. Rhalf, the sketches of Algs. 1-5, PCG (Eq. pcgsystem) and the GN loop with
+// the reuse rule of Sec. 3.2. Host code here only orchestrates: every arithmetic
+// step runs in the kernels of burgers.cu, fft.cu and dense.cu.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+#include "common.cuh"
+#include "dense.cuh"
+#include "fft.cuh"
+#include "model.cuh"
+
+namespace sc4 {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static const double kClampRel = 1e-10;  // SE prior: eigenvalues below this x max -> 0
+
+// Growable device buffer (freed explicitly by its owner).
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t b) {
+    if (b <= bytes) return SC4DVAR_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation of " + std::to_string(b) + " bytes failed");
+      return SC4DVAR_ERR_OOM;
+    }
+    bytes = b;
+    return SC4DVAR_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+enum CountMode { kOnline = 0, kOffline = 1, kKappa = 2 };
+
+}  // namespace sc4
+
+struct sc4dvar_problem_s {
+  int model = 0, n = 0, N = 0, n_t = 0, n_o = 0, m = 0;
+  double nu = 0, h = 0, sigma = 1;
+  sc4::ModelGeom geom;
+  int* obs_of_step = nullptr;
+  int* obs_idx = nullptr;
+  double* sym = nullptr;
+  double2* tw = nullptr;
+  double *xb = nullptr, *y = nullptr, *v = nullptr, *x0 = nullptr, *d = nullptr;
+  double* traj64 = nullptr;
+  float* traj32 = nullptr;
+  bool have_traj = false;
+  // scratch: block operator work arrays, reductions, small host-visible scalars
+  sc4::Buf wU, wW, wL, part, scal, vec;
+  int count_mode = sc4::kOnline;
+  sc4dvar_counters_t counters{};
+};
+
+struct sc4dvar_precond_s {
+  int n = 0, l = 0;
+  double* V = nullptr;    // n x l
+  double* lam = nullptr;  // l
+  double* dsc = nullptr;  // lam / (1 + lam)
+  sc4::Buf T;             // l x k workspace
+};
+
+namespace sc4 {
+
+using Prob = sc4dvar_problem_s;
+using Prec = sc4dvar_precond_s;
+
+static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------ small kernels
+__global__ void gaussian_kernel(uint64_t seed, uint64_t stream, int rows, int cols, int64_t col0,
+                                double* out) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t tot = (size_t)rows * cols;
+  if (idx < tot) {
+    uint64_t i = idx % rows, j = idx / rows;
+    uint64_t e = i + (uint64_t)rows * (uint64_t)(col0 + (int64_t)j);
+    out[idx] = philox_normal(seed, stream, e);
+  }
+}
+
+__global__ void fill_kernel(size_t n, double v, double* x) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(size_t n, const TI* x, TO* y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (TO)x[i];
+}
+
+// copy an r x c block (ld in) into a dense r x c (ld r) or back
+template <typename TI, typename TO>
+__global__ void copy_block_kernel(int r, int c, const TI* A, int lda, TO* B, int ldb) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx < (size_t)r * c) {
+    int i = (int)(idx % r), j = (int)(idx / r);
+    B[(size_t)j * ldb + i] = (TO)A[(size_t)j * lda + i];
+  }
+}
+
+// A = (A + A^T)/2 (+ shift I), l x l
+__global__ void symmetrize_kernel(int l, double* A, int lda, double shift) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < l * l) {
+    int i = idx % l, j = idx / l;
+    if (i < j) {
+      double a = 0.5 * (A[(size_t)j * lda + i] + A[(size_t)i * lda + j]);
+      A[(size_t)j * lda + i] = a;
+      A[(size_t)i * lda + j] = a;
+    } else if (i == j) {
+      A[(size_t)j * lda + i] += shift;
+    }
+  }
+}
+
+// B (l x r) = U[:, :r] * diag(1/sqrt(w)), and lam = max(0, w - nu) (first r)
+__global__ void svd_scale_kernel(int l, int r, const double* U, int ldu, const double* w,
+                                 double nu, double* B, double* lam, double* dsc) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < l * r) {
+    int i = idx % l, j = idx / l;
+    B[(size_t)j * l + i] = U[(size_t)j * ldu + i] / sqrt(w[j]);
+  }
+  if (idx < r) {
+    double lm = fmax(0.0, w[idx] - nu);
+    lam[idx] = lm;
+    dsc[idx] = lm / (1.0 + lm);
+  }
+}
+
+template <typename TI, typename TO>
+static int convert(size_t n, const TI* x, TO* y, cudaStream_t st) {
+  if (n == 0) return SC4DVAR_OK;
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 8 * 152);
+  convert_kernel<TI, TO><<<blocks, 256, 0, st>>>(n, x, y);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+template <typename TI, typename TO>
+static int copy_block(int r, int c, const TI* A, int lda, TO* B, int ldb, cudaStream_t st) {
+  if ((size_t)r * c == 0) return SC4DVAR_OK;
+  copy_block_kernel<TI, TO><<<(unsigned)(((size_t)r * c + 255) / 256), 256, 0, st>>>(r, c, A, lda,
+                                                                                   B, ldb);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+static int gaussian(uint64_t seed, uint64_t stream, int rows, int cols, int64_t col0, double* out,
+                    cudaStream_t st) {
+  size_t tot = (size_t)rows * cols;
+  if (tot == 0) return SC4DVAR_OK;
+  gaussian_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(seed, stream, rows, cols, col0, out);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+static int d2h(double* host, const double* dev, size_t n, cudaStream_t st) {
+  SC4_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SC4_CUDA(cudaStreamSynchronize(st));
+  return SC4DVAR_OK;
+}
+
+static void count(Prob* P, int64_t tlm, int64_t adj) {
+  switch (P->count_mode) {
+    case kOffline: P->counters.tlm_offline += tlm; P->counters.adj_offline += adj; break;
+    case kKappa: P->counters.tlm_kappa += tlm; P->counters.adj_kappa += adj; break;
+    default: P->counters.tlm_online += tlm; P->counters.adj_online += adj; break;
+  }
+}
+
+template <typename T> static const T* traj_of(Prob* P);
+template <> const double* traj_of<double>(Prob* P) { return P->traj64; }
+template <> const float* traj_of<float>(Prob* P) { return P->traj32; }
+
+// ------------------------------------------------------------------ operators
+template <typename T>
+static int tlm_block(Prob* P, const T* X, int ldx, int k, T* W, int ldw, cudaStream_t st) {
+  SC4_TRY(P->wU.ensure((size_t)P->n * k * sizeof(T)));
+  T* U = P->wU.as<T>();
+  SC4_TRY(prior_apply<T, T, T>(P->n, k, X, ldx, U, P->n, (const T*)nullptr, 0, P->sym, P->tw, st));
+  SC4_TRY(burgers_tlm<T>(P->geom, traj_of<T>(P), U, P->n, k, W, ldw, st));
+  count(P, k, 0);
+  return SC4DVAR_OK;
+}
+
+template <typename T>
+static int adj_block(Prob* P, const T* W, int ldw, int k, T* X, int ldx, const T* addZ, int ldz,
+                     cudaStream_t st) {
+  SC4_TRY(P->wL.ensure((size_t)P->n * k * sizeof(T)));
+  T* L = P->wL.as<T>();
+  SC4_TRY(burgers_adj<T>(P->geom, traj_of<T>(P), W, ldw, k, L, P->n, st));
+  SC4_TRY(prior_apply<T, T, T>(P->n, k, L, P->n, X, ldx, addZ, ldz, P->sym, P->tw, st));
+  count(P, 0, k);
+  return SC4DVAR_OK;
+}
+
+// Y = (I + A^T A) X or A^T A X, k columns, arithmetic in T.
+template <typename T>
+static int hvp_block(Prob* P, const T* X, int ldx, int k, T* Y, int ldy, int misfit_only,
+                     cudaStream_t st) {
+  SC4_TRY(P->wW.ensure((size_t)P->m * k * sizeof(T)));
+  T* W = P->wW.as<T>();
+  SC4_TRY(tlm_block<T>(P, X, ldx, k, W, P->m, st));
+  SC4_TRY(adj_block<T>(P, W, P->m, k, Y, ldy, misfit_only ? (const T*)nullptr : X, ldx, st));
+  return SC4DVAR_OK;
+}
+
+// q = (I + H) p for one FP64 vector, operator arithmetic in prec.
+static int hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t st) {
+  if (prec == SC4DVAR_FP64) return hvp_block<double>(P, p, P->n, 1, q, P->n, 0, st);
+  int n = P->n, m = P->m;
+  SC4_TRY(P->wU.ensure((size_t)n * sizeof(float)));
+  SC4_TRY(P->wW.ensure((size_t)m * sizeof(float)));
+  SC4_TRY(P->wL.ensure((size_t)n * sizeof(float)));
+  float* U = P->wU.as<float>();
+  float* W = P->wW.as<float>();
+  float* L = P->wL.as<float>();
+  SC4_TRY(prior_apply<double, float, float>(n, 1, p, n, U, n, (const float*)nullptr, 0, P->sym,
+                                            P->tw, st));
+  SC4_TRY(burgers_tlm<float>(P->geom, P->traj32, U, n, 1, W, m, st));
+  SC4_TRY(burgers_adj<float>(P->geom, P->traj32, W, m, 1, L, n, st));
+  SC4_TRY(prior_apply<float, double, double>(n, 1, L, n, q, n, p, n, P->sym, P->tw, st));
+  count(P, 1, 1);
+  return SC4DVAR_OK;
+}
+
+static int host_scalar(Prob* P, double* out, cudaStream_t st) {
+  return d2h(out, P->scal.as<double>(), 1, st);
+}
+
+// ------------------------------------------------------------------ sketch helpers
+// Workspace for the dense steps of one sketch.
+struct SketchWS {
+  Buf a, b, c, g, g2, u, w, info;
+  void release() {
+    a.release(); b.release(); c.release(); g.release(); g2.release(); u.release(); w.release();
+    info.release();
+  }
+};
+
+static int check_info(Buf& info, const char* what, cudaStream_t st) {
+  int h = 0;
+  SC4_CUDA(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SC4_CUDA(cudaStreamSynchronize(st));
+  if (h != 0) {
+    set_error(std::string(what) + ": matrix not positive definite at pivot " + std::to_string(h));
+    return SC4DVAR_ERR_NOT_SPD;
+  }
+  return SC4DVAR_OK;
+}
+
+// One CholeskyQR pass: G = src^T src (FP64), L = chol(G), dst = src L^{-T}.
+// When allowed, a failed factorization is retried with the diagonal shift
+// 11 (rows l + l(l+1)) u tr(G) (shifted CholeskyQR; tr(G) >= |G|_2).
+template <typename T>
+static int cholqr_pass(int rows, int l, const T* src, int lds, T* dst, int ldd, bool allow_shift,
+                       bool* shifted, SketchWS& ws, cudaStream_t st) {
+  SC4_TRY(ws.g.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.g2.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.info.ensure(64));
+  double* G = ws.g.as<double>();
+  double* Li = ws.g2.as<double>();
+  SC4_TRY(gemm_tn<T, T>(rows, l, l, 1.0, src, lds, src, lds, 0.0, G, l, st));
+  SC4_TRY(chol_lower(l, G, l, ws.info.as<int>(), st));
+  int s = check_info(ws.info, "CholeskyQR", st);
+  if (s == SC4DVAR_ERR_NOT_SPD && allow_shift) {
+    SC4_TRY(gemm_tn<T, T>(rows, l, l, 1.0, src, lds, src, lds, 0.0, G, l, st));
+    std::vector<double> hg((size_t)l * l);
+    SC4_CUDA(cudaMemcpyAsync(hg.data(), G, hg.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SC4_CUDA(cudaStreamSynchronize(st));
+    double tr = 0;
+    for (int i = 0; i < l; ++i) tr += hg[(size_t)i * l + i];
+    double u = (sizeof(T) == 4) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    double shift = 11.0 * ((double)rows * l + (double)l * (l + 1)) * u * tr;
+    symmetrize_kernel<<<div_up(l * l, 256), 256, 0, st>>>(l, G, l, shift);
+    SC4_LAUNCH_CHECK();
+    SC4_TRY(chol_lower(l, G, l, ws.info.as<int>(), st));
+    s = check_info(ws.info, "shifted CholeskyQR", st);
+    if (s == SC4DVAR_OK && shifted) *shifted = true;
+  }
+  if (s != SC4DVAR_OK) return s;
+  SC4_TRY(trtri_lower(l, G, l, Li, l, 0.0, st));
+  return gemm_nn<T, T>(rows, l, l, 1.0, src, lds, Li, l, 1, 0.0, dst, ldd, st);
+}
+
+// Thin QR Y = Q R by CholeskyQR2 (Q separate from Y; a third pass when the
+// first one needed a shift: shifted CholeskyQR3).
+template <typename T>
+static int cholqr2(int rows, int l, const T* Y, int ldy, T* Q, int ldq, SketchWS& ws, cudaStream_t st) {
+  bool shifted = false;
+  SC4_TRY(cholqr_pass<T>(rows, l, Y, ldy, Q, ldq, true, &shifted, ws, st));
+  SC4_TRY(ws.c.ensure((size_t)rows * l * sizeof(T)));
+  T* C = ws.c.as<T>();
+  int passes = shifted ? 2 : 1;
+  for (int p = 0; p < passes; ++p) {
+    SC4_TRY(copy_block<T, T>(rows, l, Q, ldq, C, rows, st));
+    SC4_TRY(cholqr_pass<T>(rows, l, C, rows, Q, ldq, false, nullptr, ws, st));
+  }
+  return SC4DVAR_OK;
+}
+
+// Thin SVD of W = Wt^T through the eigen-decomposition of the l x l Gram
+// Wt^T Wt (FP64 Jacobi): V = Wt U Sigma^{-1}, lam = max(0, Sigma^2 - nu).
+// Singular values below sqrt(drop) sigma_1 are dropped (their lam <= drop lam_1).
+template <typename T>
+static int finalize_svd(Prob* P, int l, const T* Wt, int ldw, double nu, double drop, Prec* out,
+                        SketchWS& ws, cudaStream_t st) {
+  int n = P->n;
+  SC4_TRY(ws.g.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.g2.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.u.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.w.ensure((size_t)4 * l * sizeof(double)));
+  double* G = ws.g.as<double>();
+  double* U = ws.g2.as<double>();
+  double* Us = ws.u.as<double>();
+  double* w = ws.w.as<double>();
+  double* ws_ = w + l;
+  SC4_TRY(gemm_tn<T, T>(n, l, l, 1.0, Wt, ldw, Wt, ldw, 0.0, G, l, st));
+  SC4_TRY(jacobi_eig(l, G, l, U, l, w, 60, 1e-15, nullptr, st));
+  SC4_TRY(sort_desc(l, w, U, l, ws_, Us, l, st));
+  std::vector<double> hw(l);
+  SC4_CUDA(cudaMemcpyAsync(hw.data(), ws_, l * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SC4_CUDA(cudaStreamSynchronize(st));
+  int r = 0;
+  while (r < l && hw[r] > drop * hw[0] && hw[r] > 0.0) ++r;
+  out->n = n;
+  out->l = r;
+  if (out->V) cudaFree(out->V);
+  if (out->lam) cudaFree(out->lam);
+  out->V = out->lam = out->dsc = nullptr;
+  if (r == 0) return SC4DVAR_OK;
+  SC4_CUDA(cudaMalloc(&out->V, (size_t)n * r * sizeof(double)));
+  SC4_CUDA(cudaMalloc(&out->lam, 2 * (size_t)r * sizeof(double)));
+  out->dsc = out->lam + r;
+  double* B = G;  // reuse: l x r
+  svd_scale_kernel<<<div_up(l * r, 256), 256, 0, st>>>(l, r, Us, l, ws_, nu, B, out->lam, out->dsc);
+  SC4_LAUNCH_CHECK();
+  SC4_TRY(gemm_nn<T, double>(n, l, r, 1.0, Wt, ldw, B, l, 0, 0.0, out->V, n, st));
+  return SC4DVAR_OK;
+}
+
+// z = (I + Wt Wt^T)^{-1} r for one vector, with L = chol(I + Wt^T Wt) given
+// as Linv = L^{-1} (Remark 1, Eq. randsvdsv): z = r - Wt Linv^T Linv Wt^T r.
+template <typename T>
+static int remark1_apply(int n, int l, const T* Wt, int ldw, const double* Linv, const double* r,
+                         double* z, double* t1, double* t2, cudaStream_t st) {
+  SC4_TRY(gemm_tn<T, double>(n, l, 1, 1.0, Wt, ldw, r, n, 0.0, t1, l, st));         // Wt^T r
+  SC4_TRY(gemm_nn<double, double>(l, l, 1, 1.0, Linv, l, t1, l, 0, 0.0, t2, l, st)); // Linv t1
+  SC4_TRY(gemm_tn<double, double>(l, l, 1, 1.0, Linv, l, t2, l, 0.0, t1, l, st));   // Linv^T t2
+  if (z != r) SC4_TRY(copy_block<double, double>(n, 1, r, n, z, n, st));
+  SC4_TRY(gemm_nn<T, double>(n, l, 1, -1.0, Wt, ldw, t1, l, 0, 1.0, z, n, st));
+  return SC4DVAR_OK;
+}
+
+// kappa = |(I + H) z| with z = P v, v the unit Philox test vector (seed, stream, col).
+static int unit_test_vector(Prob* P, uint64_t seed, uint64_t stream, int col, double* v,
+                            cudaStream_t st) {
+  SC4_TRY(gaussian(seed, stream, P->n, 1, col, v, st));
+  SC4_TRY(vnrm2<double>(P->n, v, P->scal.as<double>(), P->part.as<double>(), st));
+  double nrm;
+  SC4_TRY(host_scalar(P, &nrm, st));
+  SC4_TRY(axpby<double, double>(P->n, 0.0, v, 1.0 / nrm, v, st));
+  return SC4DVAR_OK;
+}
+
+// vec workspace: 3 n doubles (v, z, q) + 4 * lmax doubles
+static int ensure_vec(Prob* P, int lmax) {
+  return P->vec.ensure(((size_t)3 * P->n + 4 * (size_t)lmax + 64) * sizeof(double));
+}
+
+template <typename T>
+static int kappa_remark1(Prob* P, int l, const T* Wt, int ldw, uint64_t seed, uint64_t stream,
+                         int col, int prec, SketchWS& ws, double* kappa, cudaStream_t st) {
+  int n = P->n;
+  SC4_TRY(ensure_vec(P, l));
+  double* v = P->vec.as<double>();
+  double* z = v + n;
+  double* q = z + n;
+  double* t1 = q + n;
+  double* t2 = t1 + l;
+  SC4_TRY(ws.g.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.g2.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.info.ensure(64));
+  double* G = ws.g.as<double>();
+  double* Li = ws.g2.as<double>();
+  SC4_TRY(gemm_tn<T, T>(n, l, l, 1.0, Wt, ldw, Wt, ldw, 0.0, G, l, st));
+  symmetrize_kernel<<<div_up(l * l, 256), 256, 0, st>>>(l, G, l, 1.0);
+  SC4_LAUNCH_CHECK();
+  SC4_TRY(chol_lower(l, G, l, ws.info.as<int>(), st));
+  SC4_TRY(check_info(ws.info, "Remark 1 Cholesky", st));
+  SC4_TRY(trtri_lower(l, G, l, Li, l, 0.0, st));
+  SC4_TRY(unit_test_vector(P, seed, stream, col, v, st));
+  SC4_TRY(remark1_apply<T>(n, l, Wt, ldw, Li, v, z, t1, t2, st));
+  int saved = P->count_mode;
+  P->count_mode = kKappa;
+  int s = hvp_vec(P, z, q, prec, st);
+  P->count_mode = saved;
+  SC4_TRY(s);
+  SC4_TRY(vnrm2<double>(n, q, P->scal.as<double>(), P->part.as<double>(), st));
+  return host_scalar(P, kappa, st);
+}
+
+static int kappa_precond(Prob* P, Prec* pc, uint64_t seed, uint64_t stream, int col, int prec,
+                         double* kappa, cudaStream_t st) {
+  int n = P->n;
+  int l = pc ? pc->l : 0;
+  SC4_TRY(ensure_vec(P, l));
+  double* v = P->vec.as<double>();
+  double* z = v + n;
+  double* q = z + n;
+  SC4_TRY(unit_test_vector(P, seed, stream, col, v, st));
+  if (pc && l > 0) {
+    SC4_TRY(pc->T.ensure((size_t)l * sizeof(double)));
+    SC4_TRY(woodbury_apply(n, l, 1, pc->V, n, pc->dsc, v, n, z, n, pc->T.as<double>(), st));
+  } else {
+    SC4_TRY(copy_block<double, double>(n, 1, v, n, z, n, st));
+  }
+  int saved = P->count_mode;
+  P->count_mode = kKappa;
+  int s = hvp_vec(P, z, q, prec, st);
+  P->count_mode = saved;
+  SC4_TRY(s);
+  SC4_TRY(vnrm2<double>(n, q, P->scal.as<double>(), P->part.as<double>(), st));
+  return host_scalar(P, kappa, st);
+}
+
+// Draw (or copy) an rows x cols double block into a T buffer.
+template <typename T>
+static int draw_block(Prob* P, const double* given, uint64_t seed, uint64_t stream, int rows,
+                      int cols, int64_t col0, T* out, int ldo, Buf& tmp, cudaStream_t st) {
+  const double* src = given;
+  if (!src) {
+    SC4_TRY(tmp.ensure((size_t)rows * cols * sizeof(double)));
+    SC4_TRY(gaussian(seed, stream, rows, cols, col0, tmp.as<double>(), st));
+    src = tmp.as<double>();
+  }
+  return copy_block<double, T>(rows, cols, src, rows, out, ldo, st);
+}
+
+// ------------------------------------------------------------------ sketches
+template <typename T>
+static int build_randsvd(Prob* P, const sc4dvar_sketch_opts& o, const double* Om_in, Prec* out,
+                         cudaStream_t st) {
+  const int n = P->n, m = P->m;
+  const int l0 = o.l;
+  const bool adapt = o.adaptive != 0;
+  const int lh = adapt ? (o.l_hat > 0 ? o.l_hat : std::max(1, l0 / 2)) : 0;
+  const int lmax = adapt ? (o.l_max > 0 ? o.l_max : std::min(8 * l0, n)) : l0;
+  const uint64_t s_om = SC4DVAR_STREAM_SKETCH + (uint64_t)o.gn_iter;
+  const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
+  SketchWS ws;
+  Buf Om, Y, Qall, Wt, tmp;
+  int rc = SC4DVAR_OK;
+  auto body = [&]() -> int {
+    SC4_TRY(Om.ensure((size_t)n * lmax * sizeof(T)));
+    SC4_TRY(Y.ensure((size_t)m * lmax * sizeof(T)));
+    SC4_TRY(Qall.ensure((size_t)m * lmax * sizeof(T)));
+    SC4_TRY(Wt.ensure((size_t)n * lmax * sizeof(T)));
+    T* om = Om.as<T>();
+    T* y = Y.as<T>();
+    T* Q = Qall.as<T>();   // columns 0..l-1: the accumulated orthonormal basis
+    T* wt = Wt.as<T>();
+    // Alg. 1 / Alg. 4 steps 1-4
+    SC4_TRY(draw_block<T>(P, Om_in, o.seed, s_om, n, l0, 0, om, n, tmp, st));
+    SC4_TRY(tlm_block<T>(P, om, n, l0, y, m, st));
+    SC4_TRY(cholqr2<T>(m, l0, y, m, Q, m, ws, st));
+    SC4_TRY(adj_block<T>(P, Q, m, l0, wt, n, (const T*)nullptr, 0, st));
+    int l = l0;
+    if (adapt) {
+      double kap;
+      int t = 1;
+      SC4_TRY(kappa_remark1<T>(P, l, wt, n, o.seed, s_ka, t++, o.prec, ws, &kap, st));
+      while (kap > o.eps_sk && l + lh <= lmax) {
+        // Alg. 4 steps 8-14: new block, two Gram-Schmidt passes against Q, QR, ADJ
+        T* yh = y + (size_t)m * l;
+        SC4_TRY(draw_block<T>(P, nullptr, o.seed, s_om, n, lh, l, om + (size_t)n * l, n, tmp, st));
+        SC4_TRY(tlm_block<T>(P, om + (size_t)n * l, n, lh, yh, m, st));
+        SC4_TRY(ws.b.ensure((size_t)l * lh * sizeof(double)));
+        for (int pass = 0; pass < 2; ++pass) {
+          SC4_TRY(gemm_tn<T, T>(m, l, lh, 1.0, Q, m, yh, m, 0.0, ws.b.as<double>(), l, st));
+          SC4_TRY(gemm_nn<T, T>(m, l, lh, -1.0, Q, m, ws.b.as<double>(), l, 0, 1.0, yh, m, st));
+        }
+        SC4_TRY(cholqr2<T>(m, lh, yh, m, Q + (size_t)m * l, m, ws, st));
+        SC4_TRY(adj_block<T>(P, Q + (size_t)m * l, m, lh, wt + (size_t)n * l, n, (const T*)nullptr, 0, st));
+        l += lh;
+        SC4_TRY(kappa_remark1<T>(P, l, wt, n, o.seed, s_ka, t++, o.prec, ws, &kap, st));
+      }
+    }
+    double drop = (sizeof(T) == 4) ? 1e-12 : 1e-15;
+    SC4_TRY(finalize_svd<T>(P, l, wt, n, 0.0, drop, out, ws, st));
+    return SC4DVAR_OK;
+  };
+  rc = body();
+  cudaStreamSynchronize(st);
+  ws.release(); Om.release(); Y.release(); Qall.release(); Wt.release(); tmp.release();
+  return rc;
+}
+
+// Alg. 2 steps 3-7 on the sketch (Om, Y) with l columns; result into out.
+template <typename T>
+static int nystrom_core(Prob* P, int l, const T* om, T* y, double eps, Prec* out, SketchWS& ws,
+                        cudaStream_t st) {
+  const int n = P->n;
+  SC4_TRY(ws.g.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.g2.ensure((size_t)l * l * sizeof(double)));
+  SC4_TRY(ws.info.ensure(64));
+  double* G = ws.g.as<double>();
+  double* Li = ws.g2.as<double>();
+  // nu = sqrt(n) eps |Y|_2, |Y|_2^2 = lambda_max(Y^T Y)
+  SC4_TRY(gemm_tn<T, T>(n, l, l, 1.0, y, n, y, n, 0.0, G, l, st));
+  SC4_TRY(power_lmax(l, G, l, P->scal.as<double>(), st));
+  double lmax;
+  SC4_TRY(host_scalar(P, &lmax, st));
+  double nu = std::sqrt((double)n) * eps * std::sqrt(std::max(lmax, 0.0));
+  // Y <- Y + nu Omega; C = Omega^T Y; L = chol((C + C^T)/2); W^T = Y L^{-T}
+  SC4_TRY(axpby<T, T>((size_t)n * l, nu, om, 1.0, y, st));
+  SC4_TRY(gemm_tn<T, T>(n, l, l, 1.0, om, n, y, n, 0.0, G, l, st));
+  symmetrize_kernel<<<div_up(l * l, 256), 256, 0, st>>>(l, G, l, 0.0);
+  SC4_LAUNCH_CHECK();
+  SC4_TRY(chol_lower(l, G, l, ws.info.as<int>(), st));
+  SC4_TRY(check_info(ws.info, "Nystrom Cholesky", st));
+  SC4_TRY(trtri_lower(l, G, l, Li, l, 0.0, st));
+  SC4_TRY(ws.a.ensure((size_t)n * l * sizeof(T)));
+  T* wt = ws.a.as<T>();
+  SC4_TRY(gemm_nn<T, T>(n, l, l, 1.0, y, n, Li, l, 1, 0.0, wt, n, st));
+  double drop = (sizeof(T) == 4) ? 1e-12 : 1e-15;
+  return finalize_svd<T>(P, l, wt, n, nu, drop, out, ws, st);
+}
+
+template <typename T>
+static int build_nystrom(Prob* P, const sc4dvar_sketch_opts& o, const double* Om_in, Prec* out,
+                         cudaStream_t st) {
+  const int n = P->n;
+  const int l0 = o.l;
+  const bool adapt = o.adaptive != 0;
+  const int lh = adapt ? (o.l_hat > 0 ? o.l_hat : std::max(1, l0 / 2)) : 0;
+  const int lmax = adapt ? (o.l_max > 0 ? o.l_max : std::min(8 * l0, n)) : l0;
+  const uint64_t s_om = SC4DVAR_STREAM_SKETCH + (uint64_t)o.gn_iter;
+  const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
+  const double eps = (sizeof(T) == 4) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+  SketchWS ws;
+  Buf Om, Y, Yc, tmp;
+  auto body = [&]() -> int {
+    SC4_TRY(Om.ensure((size_t)n * lmax * sizeof(T)));
+    SC4_TRY(Y.ensure((size_t)n * lmax * sizeof(T)));
+    SC4_TRY(Yc.ensure((size_t)n * lmax * sizeof(T)));
+    T* om = Om.as<T>();
+    T* y = Y.as<T>();
+    T* yc = Yc.as<T>();
+    SC4_TRY(draw_block<T>(P, Om_in, o.seed, s_om, n, l0, 0, om, n, tmp, st));
+    SC4_TRY(hvp_block<T>(P, om, n, l0, y, n, 1, st));
+    int l = l0;
+    int t = 1;
+    for (;;) {
+      // the Nystrom steps shift Y in place: keep the raw sketch for growth
+      SC4_TRY(copy_block<T, T>(n, l, y, n, yc, n, st));
+      SC4_TRY(nystrom_core<T>(P, l, om, yc, eps, out, ws, st));
+      if (!adapt) break;
+      double kap;
+      SC4_TRY(kappa_precond(P, out, o.seed, s_ka, t++, o.prec, &kap, st));
+      if (!(kap > o.eps_sk) || l + lh > lmax) break;
+      SC4_TRY(draw_block<T>(P, nullptr, o.seed, s_om, n, lh, l, om + (size_t)n * l, n, tmp, st));
+      SC4_TRY(hvp_block<T>(P, om + (size_t)n * l, n, lh, y + (size_t)n * l, n, 1, st));
+      l += lh;
+    }
+    return SC4DVAR_OK;
+  };
+  int rc = body();
+  cudaStreamSynchronize(st);
+  ws.release(); Om.release(); Y.release(); Yc.release(); tmp.release();
+  return rc;
+}
+
+// Alg. 3 / Alg. 5. W = R_M^dagger (Z Q_M)^T is formed as W^T = Z M (M^T M)^{-1}
+// (= Z Q_M R_M^{-T} for M = Psi^T Q_Y = Q_M R_M of full column rank).
+template <typename T>
+static int singleview_W(Prob* P, int l1, int l2, const T* Psi, const T* QY, const T* Z, T* wt,
+                        SketchWS& ws, cudaStream_t st) {
+  const int n = P->n, m = P->m;
+  SC4_TRY(ws.b.ensure((size_t)l2 * l1 * sizeof(double)));
+  SC4_TRY(ws.g.ensure((size_t)l1 * l1 * sizeof(double)));
+  SC4_TRY(ws.g2.ensure((size_t)l1 * l1 * sizeof(double)));
+  SC4_TRY(ws.u.ensure((size_t)l2 * l1 * sizeof(double)));
+  SC4_TRY(ws.info.ensure(64));
+  double* M = ws.b.as<double>();
+  double* G = ws.g.as<double>();
+  double* Li = ws.g2.as<double>();
+  double* Bm = ws.u.as<double>();
+  SC4_TRY(gemm_tn<T, T>(m, l2, l1, 1.0, Psi, m, QY, m, 0.0, M, l2, st));       // M = Psi^T Q_Y
+  SC4_TRY(gemm_tn<double, double>(l2, l1, l1, 1.0, M, l2, M, l2, 0.0, G, l1, st));  // M^T M
+  SC4_TRY(chol_lower(l1, G, l1, ws.info.as<int>(), st));
+  SC4_TRY(check_info(ws.info, "SingleView M^T M", st));
+  SC4_TRY(trtri_lower(l1, G, l1, Li, l1, 0.0, st));
+  // Bm = M L^{-T} L^{-1}  (l2 x l1)
+  SC4_TRY(ws.w.ensure((size_t)l2 * l1 * sizeof(double)));
+  double* tmpm = ws.w.as<double>();
+  SC4_TRY(gemm_nn<double, double>(l2, l1, l1, 1.0, M, l2, Li, l1, 1, 0.0, tmpm, l2, st));
+  SC4_TRY(gemm_nn<double, double>(l2, l1, l1, 1.0, tmpm, l2, Li, l1, 0, 0.0, Bm, l2, st));
+  // W^T = Z Bm  (n x l1)
+  SC4_TRY(gemm_nn<T, T>(n, l2, l1, 1.0, Z, n, Bm, l2, 0, 0.0, wt, n, st));
+  return SC4DVAR_OK;
+}
+
+template <typename T>
+static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double* Om_in,
+                            const double* Psi_in, Prec* out, cudaStream_t st) {
+  const int n = P->n, m = P->m;
+  const int l1_0 = o.l;
+  const int l2_0 = o.l2 > 0 ? o.l2 : 2 * l1_0 + 1;
+  const bool adapt = o.adaptive != 0;
+  const int lh1 = adapt ? (o.l_hat > 0 ? o.l_hat : std::max(1, l1_0 / 2)) : 0;
+  const int lh2 = 2 * lh1;
+  const int lmax = adapt ? (o.l_max > 0 ? o.l_max : std::min(8 * l1_0, n)) : l1_0;
+  const int l2max = l2_0 + (lmax - l1_0) / std::max(1, lh1) * lh2;
+  const uint64_t s_om = SC4DVAR_STREAM_SKETCH + (uint64_t)o.gn_iter;
+  const uint64_t s_ps = s_om + SC4DVAR_STREAM_PSI;
+  const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
+  SketchWS ws;
+  Buf Om, Ps, Y, QY, Z, Wt, tmp;
+  auto body = [&]() -> int {
+    SC4_TRY(Om.ensure((size_t)n * lmax * sizeof(T)));
+    SC4_TRY(Ps.ensure((size_t)m * l2max * sizeof(T)));
+    SC4_TRY(Y.ensure((size_t)m * lmax * sizeof(T)));
+    SC4_TRY(QY.ensure((size_t)m * lmax * sizeof(T)));
+    SC4_TRY(Z.ensure((size_t)n * l2max * sizeof(T)));
+    SC4_TRY(Wt.ensure((size_t)n * lmax * sizeof(T)));
+    T *om = Om.as<T>(), *ps = Ps.as<T>(), *y = Y.as<T>(), *qy = QY.as<T>(), *z = Z.as<T>(),
+      *wt = Wt.as<T>();
+    SC4_TRY(draw_block<T>(P, Om_in, o.seed, s_om, n, l1_0, 0, om, n, tmp, st));
+    SC4_TRY(draw_block<T>(P, Psi_in, o.seed, s_ps, m, l2_0, 0, ps, m, tmp, st));
+    // Alg. 3 step 2: Y = A Omega and Z = A^T Psi (independent sweeps)
+    SC4_TRY(tlm_block<T>(P, om, n, l1_0, y, m, st));
+    SC4_TRY(adj_block<T>(P, ps, m, l2_0, z, n, (const T*)nullptr, 0, st));
+    SC4_TRY(cholqr2<T>(m, l1_0, y, m, qy, m, ws, st));
+    int l1 = l1_0, l2 = l2_0;
+    SC4_TRY(singleview_W<T>(P, l1, l2, ps, qy, z, wt, ws, st));
+    if (adapt) {
+      double kap;
+      int t = 1;
+      SC4_TRY(kappa_remark1<T>(P, l1, wt, n, o.seed, s_ka, t++, o.prec, ws, &kap, st));
+      while (kap > o.eps_sk && l1 + lh1 <= lmax) {
+        T* yh = y + (size_t)m * l1;
+        SC4_TRY(draw_block<T>(P, nullptr, o.seed, s_om, n, lh1, l1, om + (size_t)n * l1, n, tmp, st));
+        SC4_TRY(draw_block<T>(P, nullptr, o.seed, s_ps, m, lh2, l2, ps + (size_t)m * l2, m, tmp, st));
+        SC4_TRY(tlm_block<T>(P, om + (size_t)n * l1, n, lh1, yh, m, st));
+        SC4_TRY(adj_block<T>(P, ps + (size_t)m * l2, m, lh2, z + (size_t)n * l2, n, (const T*)nullptr, 0, st));
+        SC4_TRY(ws.c.ensure((size_t)l1 * lh1 * sizeof(double)));
+        for (int pass = 0; pass < 2; ++pass) {
+          SC4_TRY(gemm_tn<T, T>(m, l1, lh1, 1.0, qy, m, yh, m, 0.0, ws.c.as<double>(), l1, st));
+          SC4_TRY(gemm_nn<T, T>(m, l1, lh1, -1.0, qy, m, ws.c.as<double>(), l1, 0, 1.0, yh, m, st));
+        }
+        {
+          // QR of the new block into Q_Y's next columns (cholqr2 needs its own c buffer)
+          SketchWS ws2;
+          int s2 = cholqr2<T>(m, lh1, yh, m, qy + (size_t)m * l1, m, ws2, st);
+          cudaStreamSynchronize(st);
+          ws2.release();
+          SC4_TRY(s2);
+        }
+        l1 += lh1;
+        l2 += lh2;
+        SC4_TRY(singleview_W<T>(P, l1, l2, ps, qy, z, wt, ws, st));
+        SC4_TRY(kappa_remark1<T>(P, l1, wt, n, o.seed, s_ka, t++, o.prec, ws, &kap, st));
+      }
+    }
+    double drop = (sizeof(T) == 4) ? 1e-12 : 1e-15;
+    SC4_TRY(finalize_svd<T>(P, l1, wt, n, 0.0, drop, out, ws, st));
+    return SC4DVAR_OK;
+  };
+  int rc = body();
+  cudaStreamSynchronize(st);
+  ws.release(); Om.release(); Ps.release(); Y.release(); QY.release(); Z.release(); Wt.release();
+  tmp.release();
+  return rc;
+}
+
+// ------------------------------------------------------------------ PCG
+static int pcg_run(Prob* P, Prec* pc, const double* b, double* x, const sc4dvar_pcg_opts& o,
+                   sc4dvar_pcg_info* info, cudaStream_t st) {
+  const int n = P->n;
+  const int maxit = o.maxit > 0 ? o.maxit : n;
+  Buf wb;
+  SC4_TRY(wb.ensure((size_t)6 * n * sizeof(double)));
+  double* r = wb.as<double>();
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* e = q + n;
+  double* rhs = e + n;
+  double* sc = P->scal.as<double>();
+  double* part = P->part.as<double>();
+  if (pc && pc->l > 0) SC4_TRY(pc->T.ensure((size_t)pc->l * sizeof(double)));
+  auto precond = [&](const double* src, double* dst) -> int {
+    if (pc && pc->l > 0)
+      return woodbury_apply(n, pc->l, 1, pc->V, n, pc->dsc, src, n, dst, n, pc->T.as<double>(), st);
+    return copy_block<double, double>(n, 1, src, n, dst, n, st);
+  };
+  int total_its = 0, restarts = 0, status = SC4DVAR_OK;
+  double bnorm;
+  SC4_TRY(vnrm2<double>(n, b, sc, part, st));
+  SC4_TRY(host_scalar(P, &bnorm, st));
+  fill_kernel<<<div_up(n, 256), 256, 0, st>>>(n, 0.0, x);
+  SC4_LAUNCH_CHECK();
+  double relres = 0.0;
+  if (bnorm == 0.0) {
+    if (info) { info->iterations = 0; info->restarts = 0; info->relres = 0.0; info->status = 0; }
+    wb.release();
+    return SC4DVAR_OK;
+  }
+  const int max_restarts = (o.prec == SC4DVAR_FP32) ? std::max(0, o.refine) : 0;
+  // outer defect-correction loop: rhs = b - (I + H)_64 x; inner PCG solves for e
+  SC4_TRY(copy_block<double, double>(n, 1, b, n, rhs, n, st));
+  double rhs_norm = bnorm;
+  for (int outer = 0;; ++outer) {
+    fill_kernel<<<div_up(n, 256), 256, 0, st>>>(n, 0.0, e);
+    SC4_LAUNCH_CHECK();
+    SC4_TRY(copy_block<double, double>(n, 1, rhs, n, r, n, st));
+    SC4_TRY(precond(r, z));
+    SC4_TRY(copy_block<double, double>(n, 1, z, n, p, n, st));
+    double rz;
+    SC4_TRY(vdot<double, double>(n, r, z, sc, part, st));
+    SC4_TRY(host_scalar(P, &rz, st));
+    // inner tolerance relative to the current right-hand side
+    double tol_in = o.tol * bnorm / rhs_norm;
+    // an FP32 operator: solve a decade below the target so that one FP64 check
+    // usually suffices; the recurrence residual itself is not limited by FP32
+    if (o.prec == SC4DVAR_FP32) tol_in = std::max(0.1 * tol_in, 1e-7);
+    status = SC4DVAR_ERR_NOT_CONVERGED;
+    double rel_in = 1.0;
+    int it = 0;
+    while (it < maxit && total_its < maxit * (max_restarts + 1)) {
+      ++it;
+      ++total_its;
+      SC4_TRY(hvp_vec(P, p, q, o.prec, st));
+      double pq;
+      SC4_TRY(vdot<double, double>(n, p, q, sc, part, st));
+      SC4_TRY(host_scalar(P, &pq, st));
+      if (!(pq > 0.0) || !std::isfinite(pq)) { status = SC4DVAR_ERR_BREAKDOWN; break; }
+      double alpha = rz / pq;
+      SC4_TRY(axpby<double, double>(n, alpha, p, 1.0, e, st));
+      SC4_TRY(axpby<double, double>(n, -alpha, q, 1.0, r, st));
+      double rn;
+      SC4_TRY(vnrm2<double>(n, r, sc, part, st));
+      SC4_TRY(host_scalar(P, &rn, st));
+      rel_in = rn / rhs_norm;
+      if (rel_in <= tol_in) { status = SC4DVAR_OK; break; }
+      SC4_TRY(precond(r, z));
+      double rz_new;
+      SC4_TRY(vdot<double, double>(n, r, z, sc, part, st));
+      SC4_TRY(host_scalar(P, &rz_new, st));
+      double beta = rz_new / rz;
+      rz = rz_new;
+      SC4_TRY(axpby<double, double>(n, 1.0, z, beta, p, st));
+    }
+    SC4_TRY(axpby<double, double>(n, 1.0, e, 1.0, x, st));
+    if (o.prec != SC4DVAR_FP32) {
+      relres = rel_in * rhs_norm / bnorm;
+      break;
+    }
+    // FP64 residual of the accumulated solution (counted as one online HVP)
+    SC4_TRY(hvp_vec(P, x, q, SC4DVAR_FP64, st));
+    SC4_TRY(copy_block<double, double>(n, 1, b, n, rhs, n, st));
+    SC4_TRY(axpby<double, double>(n, -1.0, q, 1.0, rhs, st));
+    SC4_TRY(vnrm2<double>(n, rhs, sc, part, st));
+    SC4_TRY(host_scalar(P, &rhs_norm, st));
+    relres = rhs_norm / bnorm;
+    if (relres <= o.tol) { status = SC4DVAR_OK; break; }
+    if (status == SC4DVAR_ERR_BREAKDOWN || outer >= max_restarts) {
+      if (status == SC4DVAR_OK) status = SC4DVAR_ERR_NOT_CONVERGED;
+      break;
+    }
+    ++restarts;
+  }
+  if (info) {
+    info->iterations = total_its;
+    info->restarts = restarts;
+    info->relres = relres;
+    info->status = status;
+  }
+  cudaStreamSynchronize(st);
+  wb.release();
+  return SC4DVAR_OK;
+}
+
+// ------------------------------------------------------------------ model runs
+static int fwd_run(Prob* P, const double* v, double* J_host, double* d_out, cudaStream_t st) {
+  const int n = P->n, m = P->m;
+  if (v != P->v) SC4_CUDA(cudaMemcpyAsync(P->v, v, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SC4_TRY(prior_apply<double, double, double>(n, 1, P->v, n, P->x0, n, P->xb, n, P->sym, P->tw, st));
+  SC4_TRY(burgers_fwd<double>(P->geom, P->x0, P->traj64, P->traj32, P->y, P->d, nullptr, nullptr, st));
+  P->have_traj = true;
+  P->counters.fwd += 1;
+  if (d_out) SC4_CUDA(cudaMemcpyAsync(d_out, P->d, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (J_host) {
+    double a, b;
+    SC4_TRY(vdot<double, double>(n, P->v, P->v, P->scal.as<double>(), P->part.as<double>(), st));
+    SC4_TRY(host_scalar(P, &a, st));
+    SC4_TRY(vdot<double, double>(m, P->d, P->d, P->scal.as<double>(), P->part.as<double>(), st));
+    SC4_TRY(host_scalar(P, &b, st));
+    *J_host = 0.5 * a + 0.5 * b;
+  }
+  return SC4DVAR_OK;
+}
+
+static int gradient_run(Prob* P, double* g, cudaStream_t st) {
+  if (!P->have_traj) {
+    set_error("gradient: no forward trajectory (call sc4dvar_fwd first)");
+    return SC4DVAR_ERR_STATE;
+  }
+  const int n = P->n, m = P->m;
+  SC4_TRY(P->wL.ensure((size_t)n * sizeof(double)));
+  double* lam = P->wL.as<double>();
+  SC4_TRY(burgers_adj<double>(P->geom, P->traj64, P->d, m, 1, lam, n, st));
+  SC4_TRY(prior_apply<double, double, double>(n, 1, lam, n, g, n, P->v, n, P->sym, P->tw, st));
+  P->counters.adj_online += 1;
+  return SC4DVAR_OK;
+}
+
+static int build_precond_impl(Prob* P, const sc4dvar_sketch_opts& o, const double* Om,
+                              const double* Ps, Prec** out, cudaStream_t st) {
+  if (!P->have_traj) {
+    set_error("build_precond: no forward trajectory (call sc4dvar_fwd first)");
+    return SC4DVAR_ERR_STATE;
+  }
+  SC4_ARG(o.l >= 1 && o.l <= P->n, "sketch size l must be in [1, n]");
+  SC4_ARG(o.prec == SC4DVAR_FP64 || o.prec == SC4DVAR_FP32, "prec");
+  Prec* pc = new Prec();
+  int saved = P->count_mode;
+  P->count_mode = kOffline;
+  int rc;
+  bool f32 = o.prec == SC4DVAR_FP32;
+  switch (o.method) {
+    case SC4DVAR_SKETCH_RANDSVD:
+      rc = f32 ? build_randsvd<float>(P, o, Om, pc, st) : build_randsvd<double>(P, o, Om, pc, st);
+      break;
+    case SC4DVAR_SKETCH_NYSTROM:
+      rc = f32 ? build_nystrom<float>(P, o, Om, pc, st) : build_nystrom<double>(P, o, Om, pc, st);
+      break;
+    case SC4DVAR_SKETCH_SINGLEVIEW:
+      rc = f32 ? build_singleview<float>(P, o, Om, Ps, pc, st)
+               : build_singleview<double>(P, o, Om, Ps, pc, st);
+      break;
+    default:
+      set_error("unknown sketch method");
+      rc = SC4DVAR_ERR_INVALID_ARG;
+  }
+  P->count_mode = saved;
+  if (rc != SC4DVAR_OK) {
+    if (pc->V) cudaFree(pc->V);
+    if (pc->lam) cudaFree(pc->lam);
+    pc->T.release();
+    delete pc;
+    return rc;
+  }
+  *out = pc;
+  return SC4DVAR_OK;
+}
+
+static void precond_free(Prec* pc) {
+  if (!pc) return;
+  if (pc->V) cudaFree(pc->V);
+  if (pc->lam) cudaFree(pc->lam);
+  pc->T.release();
+  delete pc;
+}
+
+}  // namespace sc4
+
+// =================================================================== C ABI
+using namespace sc4;
+
+extern "C" {
+
+const char* sc4dvar_last_error(void) { return g_err.c_str(); }
+int sc4dvar_version(void) { return 100; }
+long long sc4dvar_launch_count(void) { return g_launches.load(); }
+
+int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out) {
+  SC4_ARG(d && out, "null descriptor or output");
+  SC4_ARG(d->model == SC4DVAR_MODEL_BURGERS1D, "only SC4DVAR_MODEL_BURGERS1D is supported");
+  int n = d->nx;
+  SC4_ARG(n >= 8 && n <= 8192 && (n & (n - 1)) == 0, "Burgers n must be a power of two in [8, 8192]");
+  SC4_ARG(d->n_steps >= 1 && d->dt > 0 && d->nu >= 0, "time window");
+  SC4_ARG(d->n_obs_times >= 1 && d->n_obs >= 1 && d->obs_steps && d->obs_idx, "observations");
+  SC4_ARG(d->sigma_obs > 0, "sigma_obs must be positive");
+  for (int i = 0; i < d->n_obs_times; ++i) {
+    SC4_ARG(d->obs_steps[i] >= 1 && d->obs_steps[i] <= d->n_steps, "obs_steps must lie in [1, N]");
+    SC4_ARG(i == 0 || d->obs_steps[i] > d->obs_steps[i - 1], "obs_steps must increase");
+  }
+  for (long i = 0; i < (long)d->n_obs_times * d->n_obs; ++i)
+    SC4_ARG(d->obs_idx[i] >= 0 && d->obs_idx[i] < n, "obs_idx out of range");
+  SC4_ARG(d->prior_kind == SC4DVAR_PRIOR_SE || (d->prior_kind == SC4DVAR_PRIOR_SYMBOL && d->prior_symbol),
+          "prior");
+  SC4_ARG(d->prior_kind != SC4DVAR_PRIOR_SE || (d->prior_sigma > 0 && d->prior_length > 0),
+          "SE prior parameters must be positive");
+  Prob* P = new Prob();
+  P->model = d->model;
+  P->n = n;
+  P->N = d->n_steps;
+  P->n_t = d->n_obs_times;
+  P->n_o = d->n_obs;
+  P->m = P->n_t * P->n_o;
+  P->nu = d->nu;
+  P->h = d->dt;
+  P->sigma = d->sigma_obs;
+  auto fail = [&](int code) {
+    sc4dvar_problem_destroy(P);
+    return code;
+  };
+  std::vector<int> oos(P->N + 1, -1);
+  for (int i = 0; i < P->n_t; ++i) oos[d->obs_steps[i]] = i;
+  size_t traj_pts = (size_t)(P->N + 1) * n;
+  if (cudaMalloc(&P->obs_of_step, oos.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&P->obs_idx, (size_t)P->m * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&P->sym, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->tw, (n / 2) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&P->xb, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->y, P->m * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->v, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->x0, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->d, P->m * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->traj64, traj_pts * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->traj32, traj_pts * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("problem_create: device allocation failed");
+    return fail(SC4DVAR_ERR_OOM);
+  }
+  int rc;
+  if ((rc = P->part.ensure(1024 * sizeof(double))) || (rc = P->scal.ensure(64 * sizeof(double))))
+    return fail(rc);
+  if (cudaMemcpy(P->obs_of_step, oos.data(), oos.size() * sizeof(int), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(P->obs_idx, d->obs_idx, (size_t)P->m * sizeof(int), cudaMemcpyHostToDevice) ||
+      cudaMemset(P->xb, 0, n * sizeof(double)) || cudaMemset(P->y, 0, P->m * sizeof(double)) ||
+      cudaMemset(P->v, 0, n * sizeof(double))) {
+    set_error("problem_create: copy failed");
+    return fail(SC4DVAR_ERR_CUDA);
+  }
+  P->geom.n = n;
+  P->geom.N = P->N;
+  P->geom.h = P->h;
+  P->geom.nu = P->nu;
+  P->geom.sigma = P->sigma;
+  P->geom.n_t = P->n_t;
+  P->geom.n_o = P->n_o;
+  P->geom.obs_of_step = P->obs_of_step;
+  P->geom.obs_idx = P->obs_idx;
+  if ((rc = fft_make_twiddles(n, P->tw, 0))) return fail(rc);
+  if (d->prior_kind == SC4DVAR_PRIOR_SE) {
+    if ((rc = fft_se_symbol(n, d->prior_sigma, d->prior_length, kClampRel, P->tw, P->sym, 0)))
+      return fail(rc);
+  } else {
+    if (cudaMemcpy(P->sym, d->prior_symbol, n * sizeof(double), cudaMemcpyHostToDevice)) {
+      set_error("problem_create: symbol copy failed");
+      return fail(SC4DVAR_ERR_CUDA);
+    }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error(std::string("problem_create: ") + cudaGetErrorString(cudaGetLastError()));
+    return fail(SC4DVAR_ERR_CUDA);
+  }
+  *out = P;
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_problem_destroy(sc4dvar_problem_t P) {
+  if (!P) return SC4DVAR_OK;
+  cudaFree(P->obs_of_step); cudaFree(P->obs_idx); cudaFree(P->sym); cudaFree(P->tw);
+  cudaFree(P->xb); cudaFree(P->y); cudaFree(P->v); cudaFree(P->x0); cudaFree(P->d);
+  cudaFree(P->traj64); cudaFree(P->traj32);
+  P->wU.release(); P->wW.release(); P->wL.release(); P->part.release(); P->scal.release();
+  P->vec.release();
+  delete P;
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_problem_dims(sc4dvar_problem_t P, int* n, int* m) {
+  SC4_ARG(P, "null problem");
+  if (n) *n = P->n;
+  if (m) *m = P->m;
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_set_background(sc4dvar_problem_t P, const double* xb, void* stream) {
+  SC4_ARG(P && xb, "null argument");
+  SC4_CUDA(cudaMemcpyAsync(P->xb, xb, P->n * sizeof(double), cudaMemcpyDeviceToDevice, S(stream)));
+  P->have_traj = false;
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_set_observations(sc4dvar_problem_t P, const double* y, void* stream) {
+  SC4_ARG(P && y, "null argument");
+  SC4_CUDA(cudaMemcpyAsync(P->y, y, P->m * sizeof(double), cudaMemcpyDeviceToDevice, S(stream)));
+  P->have_traj = false;
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_prior_sqrt_apply(sc4dvar_problem_t P, const double* X, int ldx, int k, double* Y,
+                             int ldy, void* stream) {
+  SC4_ARG(P && k >= 0 && (k == 0 || (X && Y)) && ldx >= P->n && ldy >= P->n, "prior_sqrt_apply arguments");
+  return prior_apply<double, double, double>(P->n, k, X, ldx, Y, ldy, (const double*)nullptr, 0,
+                                             P->sym, P->tw, S(stream));
+}
+
+int sc4dvar_prior_symbol(sc4dvar_problem_t P, double* symbol_host) {
+  SC4_ARG(P && symbol_host, "null argument");
+  SC4_CUDA(cudaMemcpy(symbol_host, P->sym, P->n * sizeof(double), cudaMemcpyDeviceToHost));
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_forecast(sc4dvar_problem_t P, const double* x0, double* obs, double* xN, void* stream) {
+  SC4_ARG(P && x0 && obs, "null argument");
+  return burgers_fwd<double>(P->geom, x0, nullptr, nullptr, nullptr, nullptr, obs, xN, S(stream));
+}
+
+int sc4dvar_fwd(sc4dvar_problem_t P, const double* v, double* J_host, double* d_dev, void* stream) {
+  SC4_ARG(P && v, "null argument");
+  return fwd_run(P, v, J_host, d_dev, S(stream));
+}
+
+int sc4dvar_gradient(sc4dvar_problem_t P, double* g, void* stream) {
+  SC4_ARG(P && g, "null argument");
+  return gradient_run(P, g, S(stream));
+}
+
+static int check_block(sc4dvar_problem_t P, int k, int prec) {
+  SC4_ARG(P, "null problem");
+  SC4_ARG(k >= 0, "k must be >= 0");
+  SC4_ARG(prec == SC4DVAR_FP64 || prec == SC4DVAR_FP32, "prec must be SC4DVAR_FP64 or SC4DVAR_FP32");
+  if (!P->have_traj) {
+    set_error("no forward trajectory (call sc4dvar_fwd first)");
+    return SC4DVAR_ERR_STATE;
+  }
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_tlm_block(sc4dvar_problem_t P, const void* X, int ldx, int k, void* W, int ldw, int prec,
+                      void* stream) {
+  SC4_TRY(check_block(P, k, prec));
+  SC4_ARG(ldx >= P->n && ldw >= P->m && (k == 0 || (X && W)), "leading dimensions / pointers");
+  if (prec == SC4DVAR_FP64)
+    return tlm_block<double>(P, (const double*)X, ldx, k, (double*)W, ldw, S(stream));
+  return tlm_block<float>(P, (const float*)X, ldx, k, (float*)W, ldw, S(stream));
+}
+
+int sc4dvar_adj_block(sc4dvar_problem_t P, const void* W, int ldw, int k, void* X, int ldx, int prec,
+                      void* stream) {
+  SC4_TRY(check_block(P, k, prec));
+  SC4_ARG(ldx >= P->n && ldw >= P->m && (k == 0 || (X && W)), "leading dimensions / pointers");
+  if (prec == SC4DVAR_FP64)
+    return adj_block<double>(P, (const double*)W, ldw, k, (double*)X, ldx, (const double*)nullptr, 0,
+                             S(stream));
+  return adj_block<float>(P, (const float*)W, ldw, k, (float*)X, ldx, (const float*)nullptr, 0,
+                          S(stream));
+}
+
+int sc4dvar_gn_hessian_apply_block(sc4dvar_problem_t P, const void* X, int ldx, int k, void* Y,
+                                   int ldy, int misfit_only, int prec, void* stream) {
+  SC4_TRY(check_block(P, k, prec));
+  SC4_ARG(ldx >= P->n && ldy >= P->n && (k == 0 || (X && Y)), "leading dimensions / pointers");
+  if (prec == SC4DVAR_FP64)
+    return hvp_block<double>(P, (const double*)X, ldx, k, (double*)Y, ldy, misfit_only, S(stream));
+  return hvp_block<float>(P, (const float*)X, ldx, k, (float*)Y, ldy, misfit_only, S(stream));
+}
+
+int sc4dvar_build_precond(sc4dvar_problem_t P, const sc4dvar_sketch_opts* o, const double* Om,
+                          const double* Ps, sc4dvar_precond_t* out, void* stream) {
+  SC4_ARG(P && o && out, "null argument");
+  return build_precond_impl(P, *o, Om, Ps, out, S(stream));
+}
+
+int sc4dvar_precond_destroy(sc4dvar_precond_t pc) {
+  precond_free(pc);
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_precond_info(sc4dvar_precond_t pc, int* rank, double* lam_host, double* V_host) {
+  SC4_ARG(pc, "null preconditioner");
+  if (rank) *rank = pc->l;
+  if (pc->l > 0) {
+    if (lam_host) SC4_CUDA(cudaMemcpy(lam_host, pc->lam, pc->l * sizeof(double), cudaMemcpyDeviceToHost));
+    if (V_host)
+      SC4_CUDA(cudaMemcpy(V_host, pc->V, (size_t)pc->n * pc->l * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_precond_apply(sc4dvar_precond_t pc, const double* R, int ldr, int k, double* Z, int ldz,
+                          void* stream) {
+  SC4_ARG(pc && k >= 0 && (k == 0 || (R && Z)) && ldr >= pc->n && ldz >= pc->n, "precond_apply arguments");
+  if (k == 0) return SC4DVAR_OK;
+  SC4_TRY(pc->T.ensure((size_t)std::max(pc->l, 1) * std::max(k, 1) * sizeof(double)));
+  return woodbury_apply(pc->n, pc->l, k, pc->V, pc->n, pc->dsc, R, ldr, Z, ldz, pc->T.as<double>(),
+                        S(stream));
+}
+
+int sc4dvar_kappa_estimate(sc4dvar_problem_t P, sc4dvar_precond_t pc, uint64_t seed,
+                           uint64_t stream_id, int column, double* kappa, void* stream) {
+  SC4_ARG(P && kappa, "null argument");
+  SC4_TRY(check_block(P, 1, SC4DVAR_FP64));
+  return kappa_precond(P, pc, seed, stream_id, column, SC4DVAR_FP64, kappa, S(stream));
+}
+
+int sc4dvar_pcg(sc4dvar_problem_t P, sc4dvar_precond_t pc, const double* b, double* x,
+                const sc4dvar_pcg_opts* o, sc4dvar_pcg_info* info, void* stream) {
+  SC4_ARG(P && b && x && o, "null argument");
+  SC4_TRY(check_block(P, 1, o->prec));
+  SC4_ARG(o->tol > 0, "tol must be positive");
+  SC4_ARG(!pc || pc->n == P->n, "preconditioner size");
+  return pcg_run(P, pc, b, x, *o, info, S(stream));
+}
+
+int sc4dvar_sketchsolv(sc4dvar_precond_t pc, const double* g, double* dv, void* stream) {
+  SC4_ARG(pc && g && dv, "null argument");
+  SC4_TRY(pc->T.ensure((size_t)std::max(pc->l, 1) * sizeof(double)));
+  SC4_TRY(woodbury_apply(pc->n, pc->l, 1, pc->V, pc->n, pc->dsc, g, pc->n, dv, pc->n,
+                         pc->T.as<double>(), S(stream)));
+  return axpby<double, double>(pc->n, 0.0, dv, -1.0, dv, S(stream));
+}
+
+int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* v_io,
+                         sc4dvar_gn_info* info, void* stream) {
+  SC4_ARG(P && o && v_io, "null argument");
+  SC4_ARG(o->iters >= 1 && o->iters <= SC4DVAR_GN_MAX_ITERS, "iters");
+  cudaStream_t st = S(stream);
+  const int n = P->n;
+  if (info) std::memset(info, 0, sizeof(*info));
+  Buf gb;
+  SC4_TRY(gb.ensure((size_t)2 * n * sizeof(double)));
+  double* g = gb.as<double>();
+  double* dv = g + n;
+  Prec* pc = nullptr;
+  double g0 = 0;
+  int rc = SC4DVAR_OK;
+  for (int k = 0; k < o->iters; ++k) {
+    double J;
+    if ((rc = fwd_run(P, v_io, &J, nullptr, st))) break;
+    if ((rc = gradient_run(P, g, st))) break;
+    double ginf;
+    if ((rc = vamax(n, g, P->scal.as<double>(), P->part.as<double>(), st))) break;
+    if ((rc = host_scalar(P, &ginf, st))) break;
+    if (k == 0) g0 = ginf;
+    if (info) {
+      info->J[k] = J;
+      info->g_inf[k] = ginf;
+      info->iters_done = k + 1;
+    }
+    if (k > 0 && o->gtol > 0 && ginf / g0 < o->gtol) break;
+    if (o->sketch.method != SC4DVAR_SKETCH_NONE) {
+      bool need = (pc == nullptr) || !o->sketch.adaptive;
+      if (!need) {
+        double kre;
+        if ((rc = kappa_precond(P, pc, o->sketch.seed, SC4DVAR_STREAM_KAPPA + k, 0, o->sketch.prec,
+                                &kre, st)))
+          break;
+        if (info) info->kappa_re[k] = kre;
+        need = !(kre < o->eps_re);
+      }
+      if (need) {
+        precond_free(pc);
+        pc = nullptr;
+        sc4dvar_sketch_opts so = o->sketch;
+        so.gn_iter = k;
+        if ((rc = build_precond_impl(P, so, nullptr, nullptr, &pc, st))) break;
+        if (info) info->sketched[k] = 1;
+      }
+      if (info) info->rank[k] = pc->l;
+    }
+    // b = -g
+    if ((rc = axpby<double, double>(n, -1.0, g, 0.0, g, st))) break;
+    sc4dvar_pcg_info pi{};
+    if ((rc = pcg_run(P, pc, g, dv, o->pcg, &pi, st))) break;
+    if (info) {
+      info->pcg_its[k] = pi.iterations;
+      info->relres[k] = pi.relres;
+    }
+    if ((rc = axpby<double, double>(n, 1.0, dv, 1.0, v_io, st))) break;
+  }
+  cudaStreamSynchronize(st);
+  precond_free(pc);
+  gb.release();
+  return rc;
+}
+
+int sc4dvar_counters(sc4dvar_problem_t P, sc4dvar_counters_t* out) {
+  SC4_ARG(P && out, "null argument");
+  *out = P->counters;
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_counters_reset(sc4dvar_problem_t P) {
+  SC4_ARG(P, "null argument");
+  P->counters = sc4dvar_counters_t{};
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, int64_t col0,
+                     double* out, void* stream) {
+  SC4_ARG(out && rows >= 0 && cols >= 0 && col0 >= 0, "gaussian arguments");
+  return gaussian(seed, stream_id, rows, cols, col0, out, S(stream));
+}
+
+}  // extern "C"

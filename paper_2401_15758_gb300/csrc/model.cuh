@@ -1,0 +1,28 @@
+#pragma once
+#include <cuda_runtime.h>
+
+namespace sc4 {
+
+// Geometry of the assimilation window shared by the model sweeps.
+struct ModelGeom {
+  int n;                    // state size
+  int N;                    // RK steps
+  double h;                 // RK step
+  double nu;                // viscosity
+  double sigma;             // observation standard deviation (R = sigma^2 I)
+  int n_t, n_o;             // observation times, sites per time
+  const int* obs_of_step;   // device [N+1]: observation index at step t, or -1
+  const int* obs_idx;       // device [n_t * n_o]
+};
+
+template <typename T>
+int burgers_fwd(const ModelGeom& g, const T* x0, T* traj, float* traj32, const double* y,
+                double* d_out, double* obs_out, T* xN, cudaStream_t st);
+template <typename T>
+int burgers_tlm(const ModelGeom& g, const T* traj, const T* U0, int ldu, int k, T* W, int ldw,
+                cudaStream_t st);
+template <typename T>
+int burgers_adj(const ModelGeom& g, const T* traj, const T* W, int ldw, int k, T* Out, int ldo,
+                cudaStream_t st);
+
+}  // namespace sc4
