@@ -105,6 +105,7 @@ SIGNATURES = {
     "sc4dvar_tlm_block": (I, [P, P, I, I, P, I, I, P]),
     "sc4dvar_adj_block": (I, [P, P, I, I, P, I, I, P]),
     "sc4dvar_gn_hessian_apply_block": (I, [P, P, I, I, P, I, I, I, P]),
+    "sc4dvar_gn_hessian_apply_block_noalloc": (I, [P, P, I, I, P, I, I, I, P]),
     "sc4dvar_build_precond": (I, [P, C.POINTER(SketchOpts), P, P, C.POINTER(P), P]),
     "sc4dvar_precond_destroy": (I, [P]),
     "sc4dvar_precond_info": (I, [P, C.POINTER(I), P, P]),

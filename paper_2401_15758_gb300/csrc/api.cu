@@ -11,6 +11,7 @@
 #include "dense.cuh"
 #include "fft.cuh"
 #include "model.cuh"
+#include "problem.cuh"
 
 namespace sc4 {
 
@@ -21,61 +22,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static const double kClampRel = 1e-10;  // SE prior: eigenvalues below this x max -> 0
 
-// Growable device buffer (freed explicitly by its owner).
-struct Buf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  int ensure(size_t b) {
-    if (b <= bytes) return SC4DVAR_OK;
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-    if (cudaMalloc(&p, b) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("device allocation of " + std::to_string(b) + " bytes failed");
-      return SC4DVAR_ERR_OOM;
-    }
-    bytes = b;
-    return SC4DVAR_OK;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  template <typename T>
-  T* as() const { return reinterpret_cast<T*>(p); }
-};
-
-enum CountMode { kOnline = 0, kOffline = 1, kKappa = 2 };
-
 }  // namespace sc4
-
-struct sc4dvar_problem_s {
-  int model = 0, n = 0, N = 0, n_t = 0, n_o = 0, m = 0;
-  double nu = 0, h = 0, sigma = 1;
-  sc4::ModelGeom geom;
-  int* obs_of_step = nullptr;
-  int* obs_idx = nullptr;
-  double* sym = nullptr;
-  double2* tw = nullptr;
-  double *xb = nullptr, *y = nullptr, *v = nullptr, *x0 = nullptr, *d = nullptr;
-  double* traj64 = nullptr;
-  float* traj32 = nullptr;
-  bool have_traj = false;
-  // scratch: block operator work arrays, reductions, small host-visible scalars
-  sc4::Buf wU, wW, wL, part, scal, vec;
-  int count_mode = sc4::kOnline;
-  sc4dvar_counters_t counters{};
-};
-
-struct sc4dvar_precond_s {
-  int n = 0, l = 0;
-  double* V = nullptr;    // n x l
-  double* lam = nullptr;  // l
-  double* dsc = nullptr;  // lam / (1 + lam)
-  sc4::Buf T;             // l x k workspace
-};
 
 namespace sc4 {
 
