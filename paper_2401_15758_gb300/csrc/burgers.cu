@@ -311,8 +311,30 @@ __global__ void __launch_bounds__(1024) burgers_adj_kernel(
   for (int p = 0; p < P; ++p) out[j0 + threadIdx.x + p * NT] = lam[p];
 }
 
+}  // namespace sc4
+
+#include "burgers_v2.cuh"
+
+namespace sc4 {
+
 // ---------------------------------------------------------------- host side
 static const size_t kMaxSmem = 227 * 1024;
+
+enum SweepKind { kFwd = 0, kTlm = 1, kAdj = 2 };
+
+// The register-resident (v2) kernels need whole warps of contiguous points.
+static bool use_v2(int seg) { return seg >= 256 && seg % 32 == 0; }
+
+static size_t sweep_smem(int kind, int seg, size_t tb) {
+  if (use_v2(seg)) {
+    size_t S = (size_t)seg + 2 * kPad;
+    if (kind == kAdj) return (4 * S + 4 * 32) * tb;
+    if (kind == kTlm) return (S + 8 * 32) * tb;
+    return (S + 4 * 32) * tb;
+  }
+  int arrays = kind == kAdj ? 6 : (kind == kTlm ? 4 : 2);
+  return (size_t)arrays * (seg + 2) * tb;
+}
 
 template <typename T>
 static BurgersParams<T> make_params(const ModelGeom& g, int seg) {
@@ -341,9 +363,9 @@ static int pick_P(int seg) {
 // Cluster size: the smallest power of two whose per-CTA shared memory fits,
 // raised for small blocks (few columns) so that one direction is spread over
 // more SMs.
-static int pick_cluster(int n, int k, size_t bytes_per_point, int arrays) {
+static int pick_cluster(int n, int k, size_t tb, int kind) {
   int cl = 1;
-  while ((size_t)arrays * (n / cl + 2) * bytes_per_point > kMaxSmem && cl < 16) cl *= 2;
+  while (sweep_smem(kind, n / cl, tb) > kMaxSmem && cl < 16) cl *= 2;
   if (k <= 4) {
     while (cl < 8 && n / (cl * 2) >= 512) cl *= 2;
   }
@@ -386,10 +408,20 @@ static int launch(Kern kern, int grid, int threads, size_t smem, int cl, cudaStr
 template <typename T>
 int burgers_fwd(const ModelGeom& g, const T* x0, T* traj, float* traj32, const double* y,
                 double* d_out, double* obs_out, T* xN, cudaStream_t st) {
-  int cl = pick_cluster(g.n, 1, sizeof(T), 2);
+  int cl = pick_cluster(g.n, 1, sizeof(T), kFwd);
   int seg = g.n / cl, P = pick_P(seg), NT = seg / P;
-  size_t smem = 2 * (size_t)(seg + 2) * sizeof(T);
+  size_t smem = sweep_smem(kFwd, seg, sizeof(T));
   auto pr = make_params<T>(g, seg);
+  if (use_v2(seg)) {
+    if (cl > 1) {
+      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_fwd_v2_kernel<T, PP, true>, cl, NT, smem, cl, st, pr,
+                                       x0, traj, traj32, y, d_out, obs_out, xN)));
+    } else {
+      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_fwd_v2_kernel<T, PP, false>, 1, NT, smem, 1, st, pr,
+                                       x0, traj, traj32, y, d_out, obs_out, xN)));
+    }
+    return SC4DVAR_OK;
+  }
   if (cl > 1) {
     SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_fwd_kernel<T, PP, true>, cl, NT, smem, cl, st, pr, x0,
                                      traj, traj32, y, d_out, obs_out, xN)));
@@ -404,10 +436,20 @@ template <typename T>
 int burgers_tlm(const ModelGeom& g, const T* traj, const T* U0, int ldu, int k, T* W, int ldw,
                 cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
-  int cl = pick_cluster(g.n, k, sizeof(T), 4);
+  int cl = pick_cluster(g.n, k, sizeof(T), kTlm);
   int seg = g.n / cl, P = pick_P(seg), NT = seg / P;
-  size_t smem = 4 * (size_t)(seg + 2) * sizeof(T);
+  size_t smem = sweep_smem(kTlm, seg, sizeof(T));
   auto pr = make_params<T>(g, seg);
+  if (use_v2(seg)) {
+    if (cl > 1) {
+      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_tlm_v2_kernel<T, PP, true>, k * cl, NT, smem, cl, st,
+                                       pr, traj, U0, ldu, W, ldw)));
+    } else {
+      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_tlm_v2_kernel<T, PP, false>, k, NT, smem, 1, st, pr,
+                                       traj, U0, ldu, W, ldw)));
+    }
+    return SC4DVAR_OK;
+  }
   if (cl > 1) {
     SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_tlm_kernel<T, PP, true>, k * cl, NT, smem, cl, st, pr,
                                      traj, U0, ldu, W, ldw)));
@@ -422,10 +464,20 @@ template <typename T>
 int burgers_adj(const ModelGeom& g, const T* traj, const T* W, int ldw, int k, T* Out, int ldo,
                 cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
-  int cl = pick_cluster(g.n, k, sizeof(T), 6);
+  int cl = pick_cluster(g.n, k, sizeof(T), kAdj);
   int seg = g.n / cl, P = pick_P(seg), NT = seg / P;
-  size_t smem = 6 * (size_t)(seg + 2) * sizeof(T);
+  size_t smem = sweep_smem(kAdj, seg, sizeof(T));
   auto pr = make_params<T>(g, seg);
+  if (use_v2(seg)) {
+    if (cl > 1) {
+      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_adj_v2_kernel<T, PP, true>, k * cl, NT, smem, cl, st,
+                                       pr, traj, W, ldw, Out, ldo)));
+    } else {
+      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_adj_v2_kernel<T, PP, false>, k, NT, smem, 1, st, pr,
+                                       traj, W, ldw, Out, ldo)));
+    }
+    return SC4DVAR_OK;
+  }
   if (cl > 1) {
     SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_adj_kernel<T, PP, true>, k * cl, NT, smem, cl, st, pr,
                                      traj, W, ldw, Out, ldo)));

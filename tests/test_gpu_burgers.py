@@ -135,3 +135,43 @@ def test_errors_are_status_codes():
     prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
     out = prob.gn_hessian_apply_block(torch.zeros((0, wl.n), dtype=torch.float64, device="cuda"))
     assert out.shape == (0, wl.n)
+
+
+# Larger grids run the register-resident kernels (contiguous points per thread,
+# shuffle halos) with and without thread-block clusters; short windows keep the
+# oracle fast while the launch shapes are the ones of the full workloads.
+V2_CASES = [
+    # (n, output steps, k, precision)
+    (8192, 20, 3, "fp32"),   # 1024 threads x 8 points, one CTA per direction
+    (8192, 20, 2, "fp64"),   # 8-CTA cluster, 1024 points per CTA (few directions)
+    (2048, 20, 5, "fp64"),   # 2 points per thread, odd k (FFT pair tail)
+    (1024, 20, 1, "fp32"),   # 2-CTA cluster
+]
+
+
+@pytest.mark.parametrize("n,n_out,k,prec", V2_CASES)
+def test_register_resident_sweeps_match_oracle(n, n_out, k, prec):
+    import paper_2401_15758_gb300 as g
+    wl = si.burgers_workload("burgers_n8192", n=n, n_out=n_out)
+    prob, ref = make_pair(wl)
+    v = 0.2 * np.random.default_rng(n).standard_normal(wl.n)
+    Jr = ref.set_iterate(v)
+    Jg = prob.fwd(torch.tensor(v, device="cuda"))
+    assert abs(Jg - Jr) <= 1e-10 * abs(Jr)
+    p = g.FP64 if prec == "fp64" else g.FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    rng = np.random.default_rng(7 + n + k)
+    X = rng.standard_normal((k, wl.n))
+    Wm = rng.standard_normal((k, wl.m))
+    A = prob.tlm_block(torch.tensor(X, device="cuda", dtype=dt), prec=p).double().cpu().numpy()
+    At = prob.adj_block(torch.tensor(Wm, device="cuda", dtype=dt), prec=p).double().cpu().numpy()
+    H = prob.gn_hessian_apply_block(torch.tensor(X, device="cuda", dtype=dt),
+                                    prec=p).double().cpu().numpy()
+    Ar, Atr, Hr = ref.A(X.T).T, ref.At(Wm.T).T, ref.hvp(X.T).T
+    for j in range(k):
+        assert rel(A[j], Ar[j]) <= tol
+        assert rel(At[j], Atr[j]) <= tol
+        assert rel(H[j], Hr[j]) <= tol
+    g_ = prob.gradient().cpu().numpy()
+    assert rel(g_, ref.gradient()) <= 1e-10
