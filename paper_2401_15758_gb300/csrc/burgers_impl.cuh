@@ -1,4 +1,6 @@
+#pragma once
 // Burgers FWD / TLM / ADJ sweeps (periodic grid, central differences, RK4).
+// Templates; instantiated for FP32 in burgers_f32.cu and FP64 in burgers_f64.cu.
 //
 // Model (Sec. 5.1, periodic reading): f_j(u) = -u_j (u_{j+1}-u_{j-1})/(2dx)
 //   + nu (u_{j+1} - 2u_j + u_{j-1})/dx^2, classic RK4 (a21 = a32 = 1/2, a43 = 1,
@@ -22,6 +24,8 @@
 // t + p*NT (p < P), so shared-memory accesses are conflict-free and global
 // accesses coalesced.
 #include <cooperative_groups.h>
+#include <algorithm>
+#include <cstdlib>
 #include "common.cuh"
 #include "model.cuh"
 
@@ -329,7 +333,7 @@ static size_t sweep_smem(int kind, int seg, size_t tb) {
   if (use_v2(seg)) {
     size_t S = (size_t)seg + 2 * kPad;
     if (kind == kAdj) return (4 * S + 4 * 32) * tb;
-    if (kind == kTlm) return (S + 8 * 32) * tb;
+    if (kind == kTlm) return (2 * (size_t)seg + S + 8 * 32) * tb;
     return (S + 4 * 32) * tb;
   }
   int arrays = kind == kAdj ? 6 : (kind == kTlm ? 4 : 2);
@@ -353,10 +357,37 @@ static BurgersParams<T> make_params(const ModelGeom& g, int seg) {
   return pr;
 }
 
-// Points per thread for a segment: NT = seg / P <= 1024 threads.
+// Points per thread for a segment: NT = seg / P <= 1024 threads. The
+// register-resident kernels take more points per thread where the segment is
+// long enough (fewer threads, per-thread overhead spread over more points);
+// SC4DVAR_SWEEP_P overrides that choice (a tuning knob: 8, 16 or 32).
 static int pick_P(int seg) {
   int P = 1;
   while (seg / P > 1024) P *= 2;
+  return P;
+}
+
+// Largest points per thread of the register-resident kernels: FP32 rows up to
+// 32 values (128 B), FP64 rows up to 4 values (32 B; longer FP64 segments are
+// split over a cluster instead).
+static int max_P_v2(size_t tb) { return tb == 4 ? 32 : 4; }
+static int threads_bound(int P, size_t tb) {
+  int bytes = P * (int)tb;
+  return bytes >= 128 ? 256 : (bytes >= 64 ? 512 : 1024);
+}
+static bool v2_fits(int seg, size_t tb) {
+  return seg / max_P_v2(tb) <= threads_bound(max_P_v2(tb), tb);
+}
+
+static int pick_P_v2(int seg, size_t tb) {
+  static int forced = [] {
+    const char* e = getenv("SC4DVAR_SWEEP_P");
+    return e ? atoi(e) : 0;
+  }();
+  int want = tb == 4 ? (forced > 0 ? std::min(forced, 32) : 16) : 4;
+  int P = 1;
+  while (P < want && seg / (2 * P) >= 256) P *= 2;
+  while (seg / P > threads_bound(P, tb) && P < max_P_v2(tb)) P *= 2;
   return P;
 }
 
@@ -365,7 +396,9 @@ static int pick_P(int seg) {
 // more SMs.
 static int pick_cluster(int n, int k, size_t tb, int kind) {
   int cl = 1;
-  while (sweep_smem(kind, n / cl, tb) > kMaxSmem && cl < 16) cl *= 2;
+  while ((sweep_smem(kind, n / cl, tb) > kMaxSmem || (use_v2(n / cl) && !v2_fits(n / cl, tb))) &&
+         cl < 16)
+    cl *= 2;
   if (k <= 4) {
     while (cl < 8 && n / (cl * 2) >= 512) cl *= 2;
   }
@@ -396,12 +429,22 @@ static int launch(Kern kern, int grid, int threads, size_t smem, int cl, cudaStr
   return SC4DVAR_OK;
 }
 
-#define SC4_DISPATCH_P(P, BODY)                                         \
+// The strided kernels only run on segments below 256 points (one point per
+// thread); the register-resident ones take 1..32 (FP32) or 1..4 (FP64) points.
+#define SC4_DISPATCH_V1(P, BODY)                                        \
+  switch (P) {                                                          \
+    case 1: { constexpr int PP = 1; BODY; } break;                      \
+    default: set_error("unsupported points per thread"); return SC4DVAR_ERR_INVALID_ARG; \
+  }
+
+#define SC4_DISPATCH_V2(T, P, BODY)                                     \
   switch (P) {                                                          \
     case 1: { constexpr int PP = 1; BODY; } break;                      \
     case 2: { constexpr int PP = 2; BODY; } break;                      \
     case 4: { constexpr int PP = 4; BODY; } break;                      \
-    case 8: { constexpr int PP = 8; BODY; } break;                      \
+    case 8: { if constexpr (sizeof(T) == 4) { constexpr int PP = 8; BODY; } } break;   \
+    case 16: { if constexpr (sizeof(T) == 4) { constexpr int PP = 16; BODY; } } break; \
+    case 32: { if constexpr (sizeof(T) == 4) { constexpr int PP = 32; BODY; } } break; \
     default: set_error("unsupported points per thread"); return SC4DVAR_ERR_INVALID_ARG; \
   }
 
@@ -409,24 +452,24 @@ template <typename T>
 int burgers_fwd(const ModelGeom& g, const T* x0, T* traj, float* traj32, const double* y,
                 double* d_out, double* obs_out, T* xN, cudaStream_t st) {
   int cl = pick_cluster(g.n, 1, sizeof(T), kFwd);
-  int seg = g.n / cl, P = pick_P(seg), NT = seg / P;
+  int seg = g.n / cl, P = use_v2(seg) ? pick_P_v2(seg, sizeof(T)) : pick_P(seg), NT = seg / P;
   size_t smem = sweep_smem(kFwd, seg, sizeof(T));
   auto pr = make_params<T>(g, seg);
   if (use_v2(seg)) {
     if (cl > 1) {
-      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_fwd_v2_kernel<T, PP, true>, cl, NT, smem, cl, st, pr,
+      SC4_DISPATCH_V2(T, P, SC4_TRY(launch(burgers_fwd_v2_kernel<T, PP, true>, cl, NT, smem, cl, st, pr,
                                        x0, traj, traj32, y, d_out, obs_out, xN)));
     } else {
-      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_fwd_v2_kernel<T, PP, false>, 1, NT, smem, 1, st, pr,
+      SC4_DISPATCH_V2(T, P, SC4_TRY(launch(burgers_fwd_v2_kernel<T, PP, false>, 1, NT, smem, 1, st, pr,
                                        x0, traj, traj32, y, d_out, obs_out, xN)));
     }
     return SC4DVAR_OK;
   }
   if (cl > 1) {
-    SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_fwd_kernel<T, PP, true>, cl, NT, smem, cl, st, pr, x0,
+    SC4_DISPATCH_V1(P, SC4_TRY(launch(burgers_fwd_kernel<T, PP, true>, cl, NT, smem, cl, st, pr, x0,
                                      traj, traj32, y, d_out, obs_out, xN)));
   } else {
-    SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_fwd_kernel<T, PP, false>, 1, NT, smem, 1, st, pr, x0,
+    SC4_DISPATCH_V1(P, SC4_TRY(launch(burgers_fwd_kernel<T, PP, false>, 1, NT, smem, 1, st, pr, x0,
                                      traj, traj32, y, d_out, obs_out, xN)));
   }
   return SC4DVAR_OK;
@@ -437,24 +480,24 @@ int burgers_tlm(const ModelGeom& g, const T* traj, const T* U0, int ldu, int k, 
                 cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
   int cl = pick_cluster(g.n, k, sizeof(T), kTlm);
-  int seg = g.n / cl, P = pick_P(seg), NT = seg / P;
+  int seg = g.n / cl, P = use_v2(seg) ? pick_P_v2(seg, sizeof(T)) : pick_P(seg), NT = seg / P;
   size_t smem = sweep_smem(kTlm, seg, sizeof(T));
   auto pr = make_params<T>(g, seg);
   if (use_v2(seg)) {
     if (cl > 1) {
-      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_tlm_v2_kernel<T, PP, true>, k * cl, NT, smem, cl, st,
+      SC4_DISPATCH_V2(T, P, SC4_TRY(launch(burgers_tlm_v2_kernel<T, PP, true>, k * cl, NT, smem, cl, st,
                                        pr, traj, U0, ldu, W, ldw)));
     } else {
-      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_tlm_v2_kernel<T, PP, false>, k, NT, smem, 1, st, pr,
+      SC4_DISPATCH_V2(T, P, SC4_TRY(launch(burgers_tlm_v2_kernel<T, PP, false>, k, NT, smem, 1, st, pr,
                                        traj, U0, ldu, W, ldw)));
     }
     return SC4DVAR_OK;
   }
   if (cl > 1) {
-    SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_tlm_kernel<T, PP, true>, k * cl, NT, smem, cl, st, pr,
+    SC4_DISPATCH_V1(P, SC4_TRY(launch(burgers_tlm_kernel<T, PP, true>, k * cl, NT, smem, cl, st, pr,
                                      traj, U0, ldu, W, ldw)));
   } else {
-    SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_tlm_kernel<T, PP, false>, k, NT, smem, 1, st, pr, traj,
+    SC4_DISPATCH_V1(P, SC4_TRY(launch(burgers_tlm_kernel<T, PP, false>, k, NT, smem, 1, st, pr, traj,
                                      U0, ldu, W, ldw)));
   }
   return SC4DVAR_OK;
@@ -465,38 +508,28 @@ int burgers_adj(const ModelGeom& g, const T* traj, const T* W, int ldw, int k, T
                 cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
   int cl = pick_cluster(g.n, k, sizeof(T), kAdj);
-  int seg = g.n / cl, P = pick_P(seg), NT = seg / P;
+  int seg = g.n / cl, P = use_v2(seg) ? pick_P_v2(seg, sizeof(T)) : pick_P(seg), NT = seg / P;
   size_t smem = sweep_smem(kAdj, seg, sizeof(T));
   auto pr = make_params<T>(g, seg);
   if (use_v2(seg)) {
     if (cl > 1) {
-      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_adj_v2_kernel<T, PP, true>, k * cl, NT, smem, cl, st,
+      SC4_DISPATCH_V2(T, P, SC4_TRY(launch(burgers_adj_v2_kernel<T, PP, true>, k * cl, NT, smem, cl, st,
                                        pr, traj, W, ldw, Out, ldo)));
     } else {
-      SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_adj_v2_kernel<T, PP, false>, k, NT, smem, 1, st, pr,
+      SC4_DISPATCH_V2(T, P, SC4_TRY(launch(burgers_adj_v2_kernel<T, PP, false>, k, NT, smem, 1, st, pr,
                                        traj, W, ldw, Out, ldo)));
     }
     return SC4DVAR_OK;
   }
   if (cl > 1) {
-    SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_adj_kernel<T, PP, true>, k * cl, NT, smem, cl, st, pr,
+    SC4_DISPATCH_V1(P, SC4_TRY(launch(burgers_adj_kernel<T, PP, true>, k * cl, NT, smem, cl, st, pr,
                                      traj, W, ldw, Out, ldo)));
   } else {
-    SC4_DISPATCH_P(P, SC4_TRY(launch(burgers_adj_kernel<T, PP, false>, k, NT, smem, 1, st, pr, traj,
+    SC4_DISPATCH_V1(P, SC4_TRY(launch(burgers_adj_kernel<T, PP, false>, k, NT, smem, 1, st, pr, traj,
                                      W, ldw, Out, ldo)));
   }
   return SC4DVAR_OK;
 }
 
-template int burgers_fwd<double>(const ModelGeom&, const double*, double*, float*, const double*,
-                                 double*, double*, double*, cudaStream_t);
-template int burgers_tlm<double>(const ModelGeom&, const double*, const double*, int, int, double*,
-                                 int, cudaStream_t);
-template int burgers_tlm<float>(const ModelGeom&, const float*, const float*, int, int, float*, int,
-                                cudaStream_t);
-template int burgers_adj<double>(const ModelGeom&, const double*, const double*, int, int, double*,
-                                 int, cudaStream_t);
-template int burgers_adj<float>(const ModelGeom&, const float*, const float*, int, int, float*, int,
-                                cudaStream_t);
 
 }  // namespace sc4
