@@ -912,6 +912,7 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   P->geom.n_o = P->n_o;
   P->geom.obs_of_step = P->obs_of_step;
   P->geom.obs_idx = P->obs_idx;
+  P->geom.fold32 = packed_f32_supported(n) ? 1 : 0;
   if ((rc = fft_make_twiddles(n, P->tw, 0))) return fail(rc);
   if (d->prior_kind == SC4DVAR_PRIOR_SE) {
     if ((rc = fft_se_symbol(n, d->prior_sigma, d->prior_length, kClampRel, P->tw, P->sym, 0)))

@@ -39,7 +39,14 @@ struct BurgersParams {
   T h, inv2dx, nudx2, inv_sigma;
   const int* obs_of_step;  // [N+1]: observation-time index at that step or -1
   const int* obs_idx;      // [n_t * n_o]
+  int fold32;              // write the FP32 trajectory copy folded (x_i, x_{i+n/2})
 };
+
+// Position of point j of a row in the folded FP32 layout (pairs x_i, x_{i+n/2}).
+__device__ __forceinline__ size_t fold_pos(int j, int n) {
+  int H = n >> 1;
+  return j < H ? (size_t)(2 * j) : (size_t)(2 * (j - H) + 1);
+}
 
 __constant__ double kRkA[3] = {0.5, 0.5, 1.0};  // a21, a32, a43
 __constant__ double kRkB[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
@@ -117,7 +124,7 @@ __global__ void __launch_bounds__(1024) burgers_fwd_kernel(
       int jl = threadIdx.x + p * NT;
       size_t g = (size_t)t * pr.n + j0 + jl;
       if (traj) traj[g] = x[p];
-      if (traj32) traj32[g] = (float)x[p];
+      if (traj32) traj32[(size_t)t * pr.n + (pr.fold32 ? fold_pos(j0 + jl, pr.n) : (size_t)(j0 + jl))] = (float)x[p];
       put<CL>(Ub[0], jl, seg, x[p], crank, csize);
     }
     bar<CL>();
@@ -354,6 +361,7 @@ static BurgersParams<T> make_params(const ModelGeom& g, int seg) {
   pr.inv_sigma = (T)(1.0 / g.sigma);
   pr.obs_of_step = g.obs_of_step;
   pr.obs_idx = g.obs_idx;
+  pr.fold32 = g.fold32;
   return pr;
 }
 
@@ -479,6 +487,9 @@ template <typename T>
 int burgers_tlm(const ModelGeom& g, const T* traj, const T* U0, int ldu, int k, T* W, int ldw,
                 cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
+  if constexpr (sizeof(T) == 4) {
+    if (g.fold32) return burgers_tlm_f32x2(g, traj, U0, ldu, k, W, ldw, st);
+  }
   int cl = pick_cluster(g.n, k, sizeof(T), kTlm);
   int seg = g.n / cl, P = use_v2(seg) ? pick_P_v2(seg, sizeof(T)) : pick_P(seg), NT = seg / P;
   size_t smem = sweep_smem(kTlm, seg, sizeof(T));
@@ -507,6 +518,9 @@ template <typename T>
 int burgers_adj(const ModelGeom& g, const T* traj, const T* W, int ldw, int k, T* Out, int ldo,
                 cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
+  if constexpr (sizeof(T) == 4) {
+    if (g.fold32) return burgers_adj_f32x2(g, traj, W, ldw, k, Out, ldo, st);
+  }
   int cl = pick_cluster(g.n, k, sizeof(T), kAdj);
   int seg = g.n / cl, P = use_v2(seg) ? pick_P_v2(seg, sizeof(T)) : pick_P(seg), NT = seg / P;
   size_t smem = sweep_smem(kAdj, seg, sizeof(T));

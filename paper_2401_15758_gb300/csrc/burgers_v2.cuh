@@ -469,7 +469,8 @@ __global__ void __launch_bounds__(Bounds<T, P>::kThreads, 1) burgers_fwd_v2_kern
     if (traj) store_row<T, P>(traj + (size_t)t * pr.n + my0, x);
     if (traj32) {
 #pragma unroll
-      for (int p = 0; p < P; ++p) traj32[(size_t)t * pr.n + my0 + p] = (float)x[p];
+      for (int p = 0; p < P; ++p)
+        traj32[(size_t)t * pr.n + (pr.fold32 ? fold_pos(my0 + p, pr.n) : (size_t)(my0 + p))] = (float)x[p];
     }
     int oi = pr.obs_of_step[t];
     if (oi >= 0) {

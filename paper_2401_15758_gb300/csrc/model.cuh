@@ -13,7 +13,17 @@ struct ModelGeom {
   int n_t, n_o;             // observation times, sites per time
   const int* obs_of_step;   // device [N+1]: observation index at step t, or -1
   const int* obs_idx;       // device [n_t * n_o]
+  int fold32 = 0;           // FP32 trajectory copy stored folded (pairs x_i, x_{i+n/2})
 };
+
+// FP32 sweeps on grids of at least this many points use packed FP32x2 kernels
+// over the folded trajectory copy.
+constexpr int kPackedMinN = 1024;
+bool packed_f32_supported(int n);
+int burgers_tlm_f32x2(const ModelGeom& m, const float* traj_folded, const float* U0, int ldu, int k,
+                      float* W, int ldw, cudaStream_t st);
+int burgers_adj_f32x2(const ModelGeom& m, const float* traj_folded, const float* Win, int ldw, int k,
+                      float* Out, int ldo, cudaStream_t st);
 
 template <typename T>
 int burgers_fwd(const ModelGeom& g, const T* x0, T* traj, float* traj32, const double* y,
