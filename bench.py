@@ -43,6 +43,12 @@ FP32_PEAK_ALU = 152 * 128 * 2 * 2.070e9   # FMA lanes x 2 flops x max SM clock (
 # recomputation not counted): TLM 52, ADJ 55.
 FLOPS_TLM = 52
 FLOPS_ADJ = 55
+KERNELS = {"tlm": "tlm_f32x2_kernel<8,false>", "adj": "adj_f32x2_kernel<8,false>"}
+# DRAM bytes (read + write) per launch of the k=128 FP32 sweeps, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the 1280-step profile case
+# (bench.py --profile), scaled by the step count to the 12 800-step launch;
+# profiles/burgers_sweeps_n8192_k128.md. Set to None when the kernels change.
+TRAFFIC_PER_LAUNCH = {"tlm": (46.179328e6 + 0.123904e6) * 10, "adj": (44.090624e6 + 0.302080e6) * 10}
 
 
 def parse():
@@ -263,9 +269,10 @@ def gpu_arm(args):
     flops = (FLOPS_ADJ if dom == "adj" else FLOPS_TLM) * wl.n * wl.n_steps * k
     achieved = flops / (kern[dom] / 1e3) / 1e12
     peak = FP32_PEAK_ALU / 1e12
-    roofline = {"bound": "alu", "kernel": f"burgers_{dom}_kernel<float>", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": KERNELS[dom], "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+                "algorithmic_bytes": wl.n_steps * wl.n * 4,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (unit counts)",
                 "kernel_ms": kern}
 
