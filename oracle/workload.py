@@ -23,3 +23,20 @@ def burgers_problem(wl, draws):
     prob.xb = draws["x_true0"] + psq(draws["xi_b"])
     prob.symbol = sym
     return prob
+
+
+def bve_problem(wl, draws):
+    """Twin experiment for the barotropic vorticity workload (Sec. 5.2 set-up on a
+    doubly periodic grid): same construction as burgers_problem."""
+    from . import bve
+    model = bve.BVE2D(wl.N, wl.nu, wl.forcing_amp, wl.forcing_k)
+    sym = bve.inv_helmholtz_sqrt_symbol(wl.N, draws["prior_c"], draws["prior_ell"])
+    psq = lambda X: bve.apply_symbol_2d(sym, X, wl.N)
+    prob = fourdvar.FourDVar(model, wl.dt, wl.n_steps, wl.obs_steps, draws["obs_idx"],
+                             draws["sigma_obs"], psq)
+    truth = prob.forward(draws["x_true0"])
+    prob.x_true_traj = truth
+    prob.y = prob.observe(truth) + draws["sigma_obs"] * draws["xi_o"]
+    prob.xb = draws["x_true0"] + psq(draws["xi_b"])
+    prob.symbol = sym
+    return prob

@@ -186,3 +186,110 @@ def describe(wl: BurgersWorkload) -> dict:
         "n_o": wl.n_obs, "m": wl.m, "k": wl.k,
     }
 
+
+
+# ---------------------------------------------------------------------------- BVE
+@dataclasses.dataclass(frozen=True)
+class BVEWorkload:
+    """Doubly periodic barotropic vorticity window on [0, 2 pi)^2 with N x N points.
+
+    The truth is normalized to max |grad^perp psi| = 1 and the RK4 step is
+    cfl * d (d = 2 pi / N). Observations: a fraction obs_frac of the grid points,
+    drawn once without replacement, observed every obs_every steps (t0 excluded).
+    Prior Gamma^{1/2} = c (I - ell^2 Lap)^{-1} with ell = ell_cells * d and
+    c = prior_frac * std(q_true0); sigma_obs = sigma_frac * max |q_true0|.
+    """
+    name: str
+    N: int
+    nu: float
+    n_steps: int
+    obs_every: int
+    obs_frac: float = 0.1
+    forcing_amp: float = 1.0
+    forcing_k: int = 4
+    k: int = 256
+    seed: int = DEFAULT_SEED
+    cfl: float = 0.2
+    ell_cells: float = 4.0
+    prior_frac: float = 0.1
+    sigma_frac: float = 0.02
+
+    @property
+    def n(self) -> int:
+        return self.N * self.N
+
+    @property
+    def d(self) -> float:
+        return 2.0 * np.pi / self.N
+
+    @property
+    def dt(self) -> float:
+        return self.cfl * self.d
+
+    @property
+    def obs_steps(self) -> np.ndarray:
+        return np.arange(self.obs_every, self.n_steps + 1, self.obs_every, dtype=np.int32)
+
+    @property
+    def n_obs_times(self) -> int:
+        return len(self.obs_steps)
+
+    @property
+    def n_obs(self) -> int:
+        return int(round(self.obs_frac * self.n))
+
+    @property
+    def m(self) -> int:
+        return self.n_obs_times * self.n_obs
+
+
+BVE_WORKLOADS = {
+    "bve_n256": BVEWorkload(name="bve_n256", N=256, nu=1e-4, n_steps=200, obs_every=10, k=256),
+    "bve_n1024": BVEWorkload(name="bve_n1024", N=1024, nu=1e-4, n_steps=256, obs_every=10, k=512),
+}
+
+
+def bve_workload(name: str, **overrides) -> BVEWorkload:
+    base = BVE_WORKLOADS[name]
+    return dataclasses.replace(base, **overrides) if overrides else base
+
+
+def _wavenumbers(N):
+    k = np.fft.fftfreq(N, 1.0 / N)
+    KY, KX = np.meshgrid(k, k, indexing="ij")
+    return KX, KY
+
+
+def bve_truth(wl: BVEWorkload) -> np.ndarray:
+    """Random vorticity with energy spectrum ~ |kappa|^-3 (amplitude of q ~ |kappa|^-1)
+    on 1 <= |kappa| <= N/3, normalized so that the velocity grad^perp psi has
+    maximum 1 (psi = Lap^{-1} q evaluated spectrally, for the normalization only)."""
+    N = wl.N
+    rng = _rng(wl.seed, STREAM_TRUTH)
+    KX, KY = _wavenumbers(N)
+    K = np.sqrt(KX ** 2 + KY ** 2)
+    band = (K >= 1.0) & (K <= N / 3.0)
+    amp = np.where(band, 1.0 / np.where(K > 0, K, 1.0), 0.0)
+    qh = amp * (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N)))
+    q = np.real(np.fft.ifft2(qh))
+    qh = np.fft.fft2(q)
+    K2 = np.where(K > 0, K ** 2, 1.0)
+    psih = np.where(K > 0, -qh / K2, 0.0)
+    u = np.real(np.fft.ifft2(-1j * KY * psih))
+    v = np.real(np.fft.ifft2(1j * KX * psih))
+    umax = np.max(np.sqrt(u ** 2 + v ** 2))
+    return (q / umax).reshape(-1)
+
+
+def bve_draws(wl: BVEWorkload) -> dict:
+    q0 = bve_truth(wl)
+    sites = np.sort(_rng(wl.seed, STREAM_OBS_SITES).choice(wl.n, size=wl.n_obs, replace=False))
+    return {
+        "x_true0": q0,
+        "xi_b": _rng(wl.seed, STREAM_BACKGROUND).standard_normal(wl.n),
+        "xi_o": _rng(wl.seed, STREAM_OBS_NOISE).standard_normal((wl.n_obs_times, wl.n_obs)),
+        "obs_idx": np.tile(sites.astype(np.int32), (wl.n_obs_times, 1)),
+        "prior_c": wl.prior_frac * float(np.std(q0)),
+        "prior_ell": wl.ell_cells * wl.d,
+        "sigma_obs": wl.sigma_frac * float(np.max(np.abs(q0))),
+    }
