@@ -59,6 +59,8 @@ extern "C" {
 
 #define SC4DVAR_PRIOR_SYMBOL    0      /* caller gives the Fourier symbol of Gamma^{1/2} */
 #define SC4DVAR_PRIOR_SE        1      /* sigma_b^2 exp(-d^2/(2 L^2)), periodic distance */
+#define SC4DVAR_PRIOR_INV_HELMHOLTZ 2  /* Gamma^{1/2} = c (I - ell^2 Lap)^{-1} on the 2D grid:
+                                          c = prior_sigma, ell = prior_length (BVE)         */
 
 #define SC4DVAR_SKETCH_NONE       0    /* Prec_Gamma: plain CG on (I + H)           */
 #define SC4DVAR_SKETCH_RANDSVD    1    /* Alg. 1 (adaptive: Alg. 4)                 */
@@ -82,7 +84,9 @@ typedef struct sc4dvar_precond_s* sc4dvar_precond_t;
 /* Problem description (all pointers are host pointers, copied at creation). */
 typedef struct {
     int model;             /* SC4DVAR_MODEL_*                                        */
-    int nx, ny;            /* grid; Burgers: n = nx (power of two, 8..16384), ny = 1 */
+    int nx, ny;            /* grid; Burgers: n = nx (power of two, 8..8192), ny = 1;
+                              BVE: nx = ny = N (power of two, 16..1024), n = N^2,
+                              fields row-major (y slow, x fast) on [0, 2 pi)^2     */
     double nu;             /* viscosity                                              */
     double dt;             /* RK4 step                                               */
     int n_steps;           /* RK4 steps in the window (N)                            */
@@ -97,6 +101,8 @@ typedef struct {
     const double* prior_symbol; /* SYMBOL: [n] real even Fourier symbol of Gamma^{1/2} */
     double forcing_amp;    /* BVE forcing amplitude (F = amp sin(k y))                */
     int forcing_k;         /* BVE forcing wavenumber                                 */
+    /* BVE (Sec. 5.2, doubly periodic form): q_t = -J_A(psi, q) + nu Lap_h q + F,
+       psi = Lap^{-1} q (spectral), J_A Arakawa's Jacobian, Lap_h five-point. */
 } sc4dvar_problem_desc;
 
 /* Sketch options (Sec. 3.1). */

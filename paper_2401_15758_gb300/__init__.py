@@ -102,19 +102,27 @@ class Problem:
     """
 
     def __init__(self, *, n, nu, dt, n_steps, obs_steps, obs_idx, sigma_obs,
-                 prior_sigma=None, prior_length=None, prior_symbol=None):
+                 prior_sigma=None, prior_length=None, prior_symbol=None, model=MODEL_BURGERS1D,
+                 grid=None, forcing_amp=0.0, forcing_k=0):
         obs_steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
         obs_idx = np.ascontiguousarray(obs_idx, dtype=np.int32)
         d = _abi.ProblemDesc()
-        d.model = MODEL_BURGERS1D
-        d.nx, d.ny = int(n), 1
+        d.model = model
+        if model == _abi.MODEL_BVE2D:
+            d.nx = d.ny = int(grid)
+            d.forcing_amp, d.forcing_k = float(forcing_amp), int(forcing_k)
+        else:
+            d.nx, d.ny = int(n), 1
         d.nu, d.dt, d.n_steps = float(nu), float(dt), int(n_steps)
         d.n_obs_times = int(obs_idx.shape[0])
         d.n_obs = int(obs_idx.shape[1])
         d.obs_steps = obs_steps.ctypes.data_as(C.POINTER(C.c_int))
         d.obs_idx = obs_idx.ctypes.data_as(C.POINTER(C.c_int))
         d.sigma_obs = float(sigma_obs)
-        if prior_symbol is not None:
+        if model == _abi.MODEL_BVE2D:
+            d.prior_kind = _abi.PRIOR_INV_HELMHOLTZ
+            d.prior_sigma, d.prior_length = float(prior_sigma), float(prior_length)
+        elif prior_symbol is not None:
             sym = np.ascontiguousarray(prior_symbol, dtype=np.float64)
             d.prior_kind = PRIOR_SYMBOL
             d.prior_symbol = sym.ctypes.data_as(C.POINTER(C.c_double))
@@ -133,6 +141,16 @@ class Problem:
         return cls(n=wl.n, nu=wl.nu, dt=wl.dt, n_steps=wl.n_steps, obs_steps=wl.obs_steps,
                    obs_idx=obs_idx, sigma_obs=wl.sigma_obs, prior_sigma=wl.sigma_b,
                    prior_length=wl.length_b, **kw)
+
+    @classmethod
+    def from_bve_workload(cls, wl, draws):
+        """Barotropic vorticity problem: N x N doubly periodic grid (fields of N*N,
+        row-major, y slow), inverse-Helmholtz prior c (I - ell^2 Lap)^{-1}."""
+        return cls(n=wl.n, nu=wl.nu, dt=wl.dt, n_steps=wl.n_steps, obs_steps=wl.obs_steps,
+                   obs_idx=draws["obs_idx"], sigma_obs=draws["sigma_obs"],
+                   prior_sigma=draws["prior_c"], prior_length=draws["prior_ell"],
+                   model=_abi.MODEL_BVE2D, grid=wl.N, forcing_amp=wl.forcing_amp,
+                   forcing_k=wl.forcing_k)
 
     def close(self):
         if getattr(self, "h", None):

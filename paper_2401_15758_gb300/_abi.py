@@ -23,6 +23,7 @@ FP64 = 0
 FP32 = 1
 PRIOR_SYMBOL = 0
 PRIOR_SE = 1
+PRIOR_INV_HELMHOLTZ = 2
 SKETCH_NONE = 0
 SKETCH_RANDSVD = 1
 SKETCH_NYSTROM = 2

@@ -3,6 +3,7 @@
 // the reuse rule of Sec. 3.2. Host code here only orchestrates: every arithmetic
 // step runs in the kernels of burgers.cu, fft.cu and dense.cu.
 #include <atomic>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -140,13 +141,44 @@ template <typename T> static const T* traj_of(Prob* P);
 template <> const double* traj_of<double>(Prob* P) { return P->traj64; }
 template <> const float* traj_of<float>(Prob* P) { return P->traj32; }
 
+static bool is_bve(const Prob* P) { return P->model == SC4DVAR_MODEL_BVE2D; }
+
+// Y = Gamma^{1/2} X (+ Z) for k columns: the 1D circulant (FFT) or the 2D
+// spectral multiplier of the model's grid.
+template <typename TI, typename TO, typename TZ>
+static int prior_any(Prob* P, int k, const TI* X, int ldx, TO* Y, int ldy, const TZ* Z, int ldz,
+                     cudaStream_t st) {
+  if (k <= 0) return SC4DVAR_OK;
+  if (!is_bve(P)) return prior_apply<TI, TO, TZ>(P->n, k, X, ldx, Y, ldy, Z, ldz, P->sym, P->tw, st);
+  constexpr bool f32 = sizeof(TI) == 4 && sizeof(TO) == 4;
+  using R = typename std::conditional<f32, float, double>::type;
+  SC4_TRY(P->wCplx.ensure((size_t)((k + 1) / 2) * P->n * 2 * sizeof(R) + 256));
+  return fft2_apply<R, TI, TO, TZ>(P->bve, k, X, ldx, Y, ldy, Z, ldz, P->bve.prior, P->wCplx.p, st);
+}
+
+// W = R^{-1/2} O_i M_i U for all i (TLM sweep of k columns)
+template <typename T>
+static int model_tlm(Prob* P, const T* U, int ldu, int k, T* W, int ldw, cudaStream_t st) {
+  if (!is_bve(P)) return burgers_tlm<T>(P->geom, traj_of<T>(P), U, ldu, k, W, ldw, st);
+  SC4_TRY(P->wBve.ensure(bve_sweep_ws_bytes(P->bve, k, sizeof(T))));
+  return bve_tlm<T>(P->bve, U, ldu, k, W, ldw, P->wBve.p, st);
+}
+
+// L = sum_i M_i^T O_i^T R^{-1/2} W_i (ADJ sweep of k columns)
+template <typename T>
+static int model_adj(Prob* P, const T* W, int ldw, int k, T* L, int ldl, cudaStream_t st) {
+  if (!is_bve(P)) return burgers_adj<T>(P->geom, traj_of<T>(P), W, ldw, k, L, ldl, st);
+  SC4_TRY(P->wBve.ensure(bve_sweep_ws_bytes(P->bve, k, sizeof(T))));
+  return bve_adj<T>(P->bve, W, ldw, k, L, ldl, P->wBve.p, st);
+}
+
 // ------------------------------------------------------------------ operators
 template <typename T>
 static int tlm_block(Prob* P, const T* X, int ldx, int k, T* W, int ldw, cudaStream_t st) {
   SC4_TRY(P->wU.ensure((size_t)P->n * k * sizeof(T)));
   T* U = P->wU.as<T>();
-  SC4_TRY(prior_apply<T, T, T>(P->n, k, X, ldx, U, P->n, (const T*)nullptr, 0, P->sym, P->tw, st));
-  SC4_TRY(burgers_tlm<T>(P->geom, traj_of<T>(P), U, P->n, k, W, ldw, st));
+  SC4_TRY(prior_any<T, T, T>(P, k, X, ldx, U, P->n, (const T*)nullptr, 0, st));
+  SC4_TRY(model_tlm<T>(P, U, P->n, k, W, ldw, st));
   count(P, k, 0);
   return SC4DVAR_OK;
 }
@@ -156,8 +188,8 @@ static int adj_block(Prob* P, const T* W, int ldw, int k, T* X, int ldx, const T
                      cudaStream_t st) {
   SC4_TRY(P->wL.ensure((size_t)P->n * k * sizeof(T)));
   T* L = P->wL.as<T>();
-  SC4_TRY(burgers_adj<T>(P->geom, traj_of<T>(P), W, ldw, k, L, P->n, st));
-  SC4_TRY(prior_apply<T, T, T>(P->n, k, L, P->n, X, ldx, addZ, ldz, P->sym, P->tw, st));
+  SC4_TRY(model_adj<T>(P, W, ldw, k, L, P->n, st));
+  SC4_TRY(prior_any<T, T, T>(P, k, L, P->n, X, ldx, addZ, ldz, st));
   count(P, 0, k);
   return SC4DVAR_OK;
 }
@@ -183,11 +215,10 @@ static int hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t s
   float* U = P->wU.as<float>();
   float* W = P->wW.as<float>();
   float* L = P->wL.as<float>();
-  SC4_TRY(prior_apply<double, float, float>(n, 1, p, n, U, n, (const float*)nullptr, 0, P->sym,
-                                            P->tw, st));
-  SC4_TRY(burgers_tlm<float>(P->geom, P->traj32, U, n, 1, W, m, st));
-  SC4_TRY(burgers_adj<float>(P->geom, P->traj32, W, m, 1, L, n, st));
-  SC4_TRY(prior_apply<float, double, double>(n, 1, L, n, q, n, p, n, P->sym, P->tw, st));
+  SC4_TRY(prior_any<double, float, float>(P, 1, p, n, U, n, (const float*)nullptr, 0, st));
+  SC4_TRY(model_tlm<float>(P, U, n, 1, W, m, st));
+  SC4_TRY(model_adj<float>(P, W, m, 1, L, n, st));
+  SC4_TRY(prior_any<float, double, double>(P, 1, L, n, q, n, p, n, st));
   count(P, 1, 1);
   return SC4DVAR_OK;
 }
@@ -754,8 +785,14 @@ static int pcg_run(Prob* P, Prec* pc, const double* b, double* x, const sc4dvar_
 static int fwd_run(Prob* P, const double* v, double* J_host, double* d_out, cudaStream_t st) {
   const int n = P->n, m = P->m;
   if (v != P->v) SC4_CUDA(cudaMemcpyAsync(P->v, v, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  SC4_TRY(prior_apply<double, double, double>(n, 1, P->v, n, P->x0, n, P->xb, n, P->sym, P->tw, st));
-  SC4_TRY(burgers_fwd<double>(P->geom, P->x0, P->traj64, P->traj32, P->y, P->d, nullptr, nullptr, st));
+  SC4_TRY(prior_any<double, double, double>(P, 1, P->v, n, P->x0, n, P->xb, n, st));
+  if (is_bve(P)) {
+    SC4_TRY(P->wBve.ensure(std::max(bve_fwd_ws_bytes(P->bve), bve_sweep_ws_bytes(P->bve, 1, 8))));
+    SC4_TRY(bve_fwd(P->bve, P->x0, P->bve_q64, P->bve_p64, P->bve_q32, P->bve_p32, P->y, P->d, nullptr,
+                    nullptr, P->wBve.p, st));
+  } else {
+    SC4_TRY(burgers_fwd<double>(P->geom, P->x0, P->traj64, P->traj32, P->y, P->d, nullptr, nullptr, st));
+  }
   P->have_traj = true;
   P->counters.fwd += 1;
   if (d_out) SC4_CUDA(cudaMemcpyAsync(d_out, P->d, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -778,8 +815,8 @@ static int gradient_run(Prob* P, double* g, cudaStream_t st) {
   const int n = P->n, m = P->m;
   SC4_TRY(P->wL.ensure((size_t)n * sizeof(double)));
   double* lam = P->wL.as<double>();
-  SC4_TRY(burgers_adj<double>(P->geom, P->traj64, P->d, m, 1, lam, n, st));
-  SC4_TRY(prior_apply<double, double, double>(n, 1, lam, n, g, n, P->v, n, P->sym, P->tw, st));
+  SC4_TRY(model_adj<double>(P, P->d, m, 1, lam, n, st));
+  SC4_TRY(prior_any<double, double, double>(P, 1, lam, n, g, n, P->v, n, st));
   P->counters.adj_online += 1;
   return SC4DVAR_OK;
 }
@@ -845,9 +882,18 @@ long long sc4dvar_launch_count(void) { return g_launches.load(); }
 
 int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out) {
   SC4_ARG(d && out, "null descriptor or output");
-  SC4_ARG(d->model == SC4DVAR_MODEL_BURGERS1D, "only SC4DVAR_MODEL_BURGERS1D is supported");
-  int n = d->nx;
-  SC4_ARG(n >= 8 && n <= 8192 && (n & (n - 1)) == 0, "Burgers n must be a power of two in [8, 8192]");
+  SC4_ARG(d->model == SC4DVAR_MODEL_BURGERS1D || d->model == SC4DVAR_MODEL_BVE2D, "unknown model");
+  const bool bve = d->model == SC4DVAR_MODEL_BVE2D;
+  if (bve) {
+    SC4_ARG(d->nx == d->ny && d->nx >= 16 && d->nx <= 1024 && (d->nx & (d->nx - 1)) == 0,
+            "BVE grid must be N x N with N a power of two in [16, 1024]");
+    SC4_ARG(d->prior_kind == SC4DVAR_PRIOR_INV_HELMHOLTZ && d->prior_sigma > 0 && d->prior_length >= 0,
+            "BVE prior: SC4DVAR_PRIOR_INV_HELMHOLTZ with prior_sigma > 0, prior_length >= 0");
+  } else {
+    SC4_ARG(d->nx >= 8 && d->nx <= 8192 && (d->nx & (d->nx - 1)) == 0,
+            "Burgers n must be a power of two in [8, 8192]");
+  }
+  int n = bve ? d->nx * d->ny : d->nx;
   SC4_ARG(d->n_steps >= 1 && d->dt > 0 && d->nu >= 0, "time window");
   SC4_ARG(d->n_obs_times >= 1 && d->n_obs >= 1 && d->obs_steps && d->obs_idx, "observations");
   SC4_ARG(d->sigma_obs > 0, "sigma_obs must be positive");
@@ -857,7 +903,8 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   }
   for (long i = 0; i < (long)d->n_obs_times * d->n_obs; ++i)
     SC4_ARG(d->obs_idx[i] >= 0 && d->obs_idx[i] < n, "obs_idx out of range");
-  SC4_ARG(d->prior_kind == SC4DVAR_PRIOR_SE || (d->prior_kind == SC4DVAR_PRIOR_SYMBOL && d->prior_symbol),
+  SC4_ARG(bve || d->prior_kind == SC4DVAR_PRIOR_SE ||
+              (d->prior_kind == SC4DVAR_PRIOR_SYMBOL && d->prior_symbol),
           "prior");
   SC4_ARG(d->prior_kind != SC4DVAR_PRIOR_SE || (d->prior_sigma > 0 && d->prior_length > 0),
           "SE prior parameters must be positive");
@@ -877,18 +924,35 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   };
   std::vector<int> oos(P->N + 1, -1);
   for (int i = 0; i < P->n_t; ++i) oos[d->obs_steps[i]] = i;
-  size_t traj_pts = (size_t)(P->N + 1) * n;
+  P->obs_of_step_h = oos;
+  size_t traj_pts = bve ? 0 : (size_t)(P->N + 1) * n;
+  if (bve) {
+    const int Ng = d->nx;
+    size_t stages = (size_t)4 * P->N * n;
+    if (cudaMalloc(&P->bve_tw64, (Ng / 2) * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&P->bve_tw32, (Ng / 2) * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&P->bve_poisson, (size_t)n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P->bve_prior, (size_t)n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P->bve_q64, stages * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P->bve_p64, stages * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P->bve_q32, stages * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&P->bve_p32, stages * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("problem_create: device allocation of the BVE stage states failed");
+      return fail(SC4DVAR_ERR_OOM);
+    }
+  }
   if (cudaMalloc(&P->obs_of_step, oos.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&P->obs_idx, (size_t)P->m * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&P->sym, n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&P->tw, (n / 2) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&P->sym, (bve ? 1 : n) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->tw, (bve ? 1 : n / 2) * sizeof(double2)) != cudaSuccess ||
       cudaMalloc(&P->xb, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->y, P->m * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->v, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->x0, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->d, P->m * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&P->traj64, traj_pts * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&P->traj32, traj_pts * sizeof(float)) != cudaSuccess) {
+      (!bve && cudaMalloc(&P->traj64, traj_pts * sizeof(double)) != cudaSuccess) ||
+      (!bve && cudaMalloc(&P->traj32, traj_pts * sizeof(float)) != cudaSuccess)) {
     cudaGetLastError();
     set_error("problem_create: device allocation failed");
     return fail(SC4DVAR_ERR_OOM);
@@ -912,9 +976,37 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   P->geom.n_o = P->n_o;
   P->geom.obs_of_step = P->obs_of_step;
   P->geom.obs_idx = P->obs_idx;
-  P->geom.fold32 = packed_f32_supported(n) ? 1 : 0;
-  if ((rc = fft_make_twiddles(n, P->tw, 0))) return fail(rc);
-  if (d->prior_kind == SC4DVAR_PRIOR_SE) {
+  P->geom.fold32 = (!bve && packed_f32_supported(n)) ? 1 : 0;
+  if (bve) {
+    BveGeom& b = P->bve;
+    b.N = d->nx;
+    b.Nsteps = P->N;
+    b.n_t = P->n_t;
+    b.n_o = P->n_o;
+    b.h = P->h;
+    b.nu = P->nu;
+    b.sigma = P->sigma;
+    b.famp = d->forcing_amp;
+    b.fk = d->forcing_k;
+    b.prior_c = d->prior_sigma;
+    b.prior_ell = d->prior_length;
+    b.obs_of_step_h = P->obs_of_step_h.data();
+    b.obs_idx = P->obs_idx;
+    b.tw64 = P->bve_tw64;
+    b.tw32 = P->bve_tw32;
+    b.poisson = P->bve_poisson;
+    b.prior = P->bve_prior;
+    b.q64 = P->bve_q64;
+    b.p64 = P->bve_p64;
+    b.q32 = P->bve_q32;
+    b.p32 = P->bve_p32;
+    if ((rc = bve_setup(b, 0))) return fail(rc);
+  } else if ((rc = fft_make_twiddles(n, P->tw, 0))) {
+    return fail(rc);
+  }
+  if (bve) {
+    // prior handled by the 2D multiplier
+  } else if (d->prior_kind == SC4DVAR_PRIOR_SE) {
     if ((rc = fft_se_symbol(n, d->prior_sigma, d->prior_length, kClampRel, P->tw, P->sym, 0)))
       return fail(rc);
   } else {
@@ -936,6 +1028,9 @@ int sc4dvar_problem_destroy(sc4dvar_problem_t P) {
   cudaFree(P->obs_of_step); cudaFree(P->obs_idx); cudaFree(P->sym); cudaFree(P->tw);
   cudaFree(P->xb); cudaFree(P->y); cudaFree(P->v); cudaFree(P->x0); cudaFree(P->d);
   cudaFree(P->traj64); cudaFree(P->traj32);
+  cudaFree(P->bve_tw64); cudaFree(P->bve_tw32); cudaFree(P->bve_poisson); cudaFree(P->bve_prior);
+  cudaFree(P->bve_q64); cudaFree(P->bve_p64); cudaFree(P->bve_q32); cudaFree(P->bve_p32);
+  P->wBve.release(); P->wCplx.release();
   P->wU.release(); P->wW.release(); P->wL.release(); P->part.release(); P->scal.release();
   P->vec.release();
   delete P;
@@ -966,18 +1061,26 @@ int sc4dvar_set_observations(sc4dvar_problem_t P, const double* y, void* stream)
 int sc4dvar_prior_sqrt_apply(sc4dvar_problem_t P, const double* X, int ldx, int k, double* Y,
                              int ldy, void* stream) {
   SC4_ARG(P && k >= 0 && (k == 0 || (X && Y)) && ldx >= P->n && ldy >= P->n, "prior_sqrt_apply arguments");
-  return prior_apply<double, double, double>(P->n, k, X, ldx, Y, ldy, (const double*)nullptr, 0,
-                                             P->sym, P->tw, S(stream));
+  return prior_any<double, double, double>(P, k, X, ldx, Y, ldy, (const double*)nullptr, 0, S(stream));
 }
 
 int sc4dvar_prior_symbol(sc4dvar_problem_t P, double* symbol_host) {
   SC4_ARG(P && symbol_host, "null argument");
+  if (is_bve(P)) {
+    SC4_CUDA(cudaMemcpy(symbol_host, P->bve.prior, P->n * sizeof(double), cudaMemcpyDeviceToHost));
+    return SC4DVAR_OK;
+  }
   SC4_CUDA(cudaMemcpy(symbol_host, P->sym, P->n * sizeof(double), cudaMemcpyDeviceToHost));
   return SC4DVAR_OK;
 }
 
 int sc4dvar_forecast(sc4dvar_problem_t P, const double* x0, double* obs, double* xN, void* stream) {
   SC4_ARG(P && x0 && obs, "null argument");
+  if (is_bve(P)) {
+    SC4_TRY(P->wBve.ensure(std::max(bve_fwd_ws_bytes(P->bve), P->wBve.bytes)));
+    return bve_fwd(P->bve, x0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, obs, xN, P->wBve.p,
+                   S(stream));
+  }
   return burgers_fwd<double>(P->geom, x0, nullptr, nullptr, nullptr, nullptr, obs, xN, S(stream));
 }
 

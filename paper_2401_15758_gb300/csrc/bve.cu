@@ -1,0 +1,602 @@
+// Barotropic vorticity model: FWD / TLM / ADJ sweeps and the 2D FFT multiplier.
+//
+// Model (doubly periodic [0, 2 pi)^2, N x N points, d = 2 pi / N; the workload
+// form of the paper's Sec. 5.2 equation):
+//   q_t = -J_A(psi, q) + nu Lap_h q + a sin(k_f y),   psi = Lap^{-1} q (spectral)
+// with J_A Arakawa's nine-point Jacobian and Lap_h the five-point Laplacian.
+// TLM stage:  dk = -J_A(Lap^{-1} dq, q) - J_A(psi, dq) + nu Lap_h dq
+// ADJ stage:  theta = -Lap^{-1} J_A(q, kappa) + J_A(psi, kappa) + nu Lap_h kappa
+// (exact transposes: Lap^{-1}, Lap_h symmetric; J_A antisymmetric in its two
+// arguments and skew-symmetric in the second), inside the same discrete RK4
+// adjoint as the Burgers sweeps.
+//
+// GB300 mapping. The field of one direction (N^2 up to 1M points) does not fit
+// one SM, so the sweeps stream: per RK stage, batched kernels over all k
+// directions -- a 2D FFT multiplier (Poisson solve) and one stencil kernel --
+// with the base stage states q_s, psi_s stored by the FWD and shared by all
+// directions through L2. Fields are row-major (y slow, x fast).
+//
+// 2D FFT multiplier Y = IFFT2(S . FFT2(X)) with a real, even symbol S: two real
+// fields are transformed together as one complex field (the multiplier maps
+// real fields to real fields). Three kernels: row FFTs; column FFT, symbol,
+// inverse column FFT (one pass); inverse row FFTs. Radix-2 in shared memory with
+// a per-problem twiddle table.
+#include <algorithm>
+#include <cmath>
+#include "bve.cuh"
+#include "common.cuh"
+
+namespace sc4 {
+
+template <typename C> struct CplxOf;
+template <> struct CplxOf<float2> { using R = float; };
+template <> struct CplxOf<double2> { using R = double; };
+template <typename R> struct CplxT;
+template <> struct CplxT<float> { using C = float2; };
+template <> struct CplxT<double> { using C = double2; };
+
+template <typename C>
+__device__ __forceinline__ C cmk(typename CplxOf<C>::R x, typename CplxOf<C>::R y) { C c; c.x = x; c.y = y; return c; }
+template <typename C>
+__device__ __forceinline__ C cmulc(C a, C b) { return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+__device__ __forceinline__ unsigned brev_n(unsigned j, int logn) { return __brev(j) >> (32 - logn); }
+
+// Radix-2 transforms of `nb` sequences of length N in shared memory; element
+// (b, i) at s[b * sb + i * si]. DIT: bit-reversed in, natural out. DIF: natural
+// in, bit-reversed out. dir = -1 forward, +1 inverse (unscaled). Work items are
+// ordered so that consecutive threads touch consecutive addresses.
+template <typename C, bool DIT>
+__device__ void fft_batch(C* s, int N, int nb, int sb, int si, bool b_fast, const C* __restrict__ tw,
+                          int dir) {
+  const int nbf = N / 2;
+  for (int step = 0, half = DIT ? 1 : N / 2; step < 32 && half >= 1 && half < N;
+       ++step, half = DIT ? half * 2 : half / 2) {
+    const int stride = N / (2 * half);
+    __syncthreads();
+    for (int it = threadIdx.x; it < nb * nbf; it += blockDim.x) {
+      int b, bf;
+      if (b_fast) { b = it % nb; bf = it / nb; }
+      else { bf = it % nbf; b = it / nbf; }
+      int grp = bf / half, kk = bf - grp * half;
+      int i0 = grp * 2 * half + kk, i1 = i0 + half;
+      C w = tw[kk * stride];
+      if (dir > 0) w.y = -w.y;
+      C* p0 = s + b * sb + i0 * si;
+      C* p1 = s + b * sb + i1 * si;
+      C u = *p0, v = *p1;
+      if (DIT) {
+        C t = cmulc(w, v);
+        *p0 = cmk<C>(u.x + t.x, u.y + t.y);
+        *p1 = cmk<C>(u.x - t.x, u.y - t.y);
+      } else {
+        *p0 = cmk<C>(u.x + v.x, u.y + v.y);
+        *p1 = cmulc(w, cmk<C>(u.x - v.x, u.y - v.y));
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// rows, forward: fields (2p, 2p+1) -> complex rows (natural kx), RB rows per CTA
+template <typename C, typename RI>
+__global__ void fft2_rows_fwd(int N, int logN, int k, const RI* __restrict__ X, int ldx, C* cbuf,
+                              const C* __restrict__ tw, int RB) {
+  using R = typename CplxOf<C>::R;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tile = reinterpret_cast<C*>(smraw);  // [RB][N]
+  const int p = blockIdx.y, fa = 2 * p, fb = 2 * p + 1;
+  const int j0 = blockIdx.x * RB;
+  const RI* xa = X + (size_t)fa * ldx;
+  const RI* xb = X + (size_t)fb * ldx;
+  const bool hasb = fb < k;
+  for (int it = threadIdx.x; it < RB * N; it += blockDim.x) {
+    int r = it / N, i = it - r * N;
+    size_t g = (size_t)(j0 + r) * N + i;
+    tile[r * N + brev_n(i, logN)] = cmk<C>((R)xa[g], hasb ? (R)xb[g] : (R)0);
+  }
+  fft_batch<C, true>(tile, N, RB, N, 1, false, tw, -1);
+  C* out = cbuf + (size_t)p * N * N;
+  for (int it = threadIdx.x; it < RB * N; it += blockDim.x) {
+    int r = it / N, i = it - r * N;
+    out[(size_t)(j0 + r) * N + i] = tile[r * N + i];
+  }
+}
+
+// columns: forward FFT along y, multiply by the symbol, inverse FFT along y
+template <typename C>
+__global__ void fft2_cols(int N, int logN, C* cbuf, const double* __restrict__ table,
+                          const C* __restrict__ tw, int CB) {
+  using R = typename CplxOf<C>::R;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tile = reinterpret_cast<C*>(smraw);  // [N][CB+1]
+  const int ld = CB + 1;
+  const int p = blockIdx.y;
+  const int i0 = blockIdx.x * CB;
+  C* g = cbuf + (size_t)p * N * N;
+  for (int it = threadIdx.x; it < N * CB; it += blockDim.x) {
+    int j = it / CB, c = it - j * CB;
+    tile[brev_n(j, logN) * ld + c] = g[(size_t)j * N + i0 + c];
+  }
+  fft_batch<C, true>(tile, N, CB, 1, ld, true, tw, -1);
+  for (int it = threadIdx.x; it < N * CB; it += blockDim.x) {
+    int j = it / CB, c = it - j * CB;
+    R s = (R)table[(size_t)j * N + i0 + c];
+    C v = tile[j * ld + c];
+    tile[j * ld + c] = cmk<C>(v.x * s, v.y * s);
+  }
+  fft_batch<C, false>(tile, N, CB, 1, ld, true, tw, +1);
+  for (int it = threadIdx.x; it < N * CB; it += blockDim.x) {
+    int j = it / CB, c = it - j * CB;
+    g[(size_t)j * N + i0 + c] = tile[brev_n(j, logN) * ld + c];
+  }
+}
+
+// rows, inverse: complex rows -> fields (2p, 2p+1), scaled by 1/N^2 (+ Z)
+template <typename C, typename RO, typename RZ>
+__global__ void fft2_rows_inv(int N, int logN, int k, const C* cbuf, RO* __restrict__ Y, int ldy,
+                              const RZ* __restrict__ Z, int ldz, const C* __restrict__ tw, int RB) {
+  using R = typename CplxOf<C>::R;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tile = reinterpret_cast<C*>(smraw);
+  const int p = blockIdx.y, fa = 2 * p, fb = 2 * p + 1;
+  const int j0 = blockIdx.x * RB;
+  const bool hasb = fb < k;
+  const C* in = cbuf + (size_t)p * N * N;
+  for (int it = threadIdx.x; it < RB * N; it += blockDim.x) {
+    int r = it / N, i = it - r * N;
+    tile[r * N + i] = in[(size_t)(j0 + r) * N + i];
+  }
+  fft_batch<C, false>(tile, N, RB, N, 1, false, tw, +1);
+  const R scale = (R)1 / ((R)N * (R)N);
+  for (int it = threadIdx.x; it < RB * N; it += blockDim.x) {
+    int r = it / N, i = it - r * N;
+    size_t gi = (size_t)(j0 + r) * N + i;
+    C v = tile[r * N + brev_n(i, logN)];
+    R a = v.x * scale, b = v.y * scale;
+    if (Z) {
+      a += (R)Z[(size_t)fa * ldz + gi];
+      if (hasb) b += (R)Z[(size_t)fb * ldz + gi];
+    }
+    Y[(size_t)fa * ldy + gi] = (RO)a;
+    if (hasb) Y[(size_t)fb * ldy + gi] = (RO)b;
+  }
+}
+
+__global__ void bve_twiddle_kernel(int N, double2* tw64, float2* tw32) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < N / 2) {
+    double s, c;
+    sincospi(-2.0 * (double)j / (double)N, &s, &c);
+    tw64[j] = make_double2(c, s);
+    tw32[j] = make_float2((float)c, (float)s);
+  }
+}
+
+// kind 0: Poisson -1/|kappa|^2 (0 at kappa = 0); kind 1: c / (1 + ell^2 |kappa|^2)
+__global__ void bve_table_kernel(int N, int kind, double c, double ell, double* table) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx < (size_t)N * N) {
+    int j = (int)(idx / N), i = (int)(idx % N);
+    double kx = (i < N / 2) ? i : i - N;
+    double ky = (j < N / 2) ? j : j - N;
+    double k2 = kx * kx + ky * ky;
+    table[idx] = (kind == 0) ? (k2 > 0 ? -1.0 / k2 : 0.0) : c / (1.0 + ell * ell * k2);
+  }
+}
+
+// ------------------------------------------------------------------ stencils
+template <typename T>
+struct St9 {
+  T c, e, w, n, s, ne, nw, se, sw;
+};
+
+template <typename T>
+__device__ __forceinline__ St9<T> ld9(const T* __restrict__ f, int N, int i, int j) {
+  const int ip = (i + 1) & (N - 1), im = (i - 1) & (N - 1);
+  const int jp = (j + 1) & (N - 1), jm = (j - 1) & (N - 1);
+  St9<T> v;
+  const T* r0 = f + (size_t)j * N;
+  const T* rp = f + (size_t)jp * N;
+  const T* rm = f + (size_t)jm * N;
+  v.c = __ldg(r0 + i); v.e = __ldg(r0 + ip); v.w = __ldg(r0 + im);
+  v.n = __ldg(rp + i); v.s = __ldg(rm + i);
+  v.ne = __ldg(rp + ip); v.nw = __ldg(rp + im); v.se = __ldg(rm + ip); v.sw = __ldg(rm + im);
+  return v;
+}
+
+// Arakawa J_A(a, b) times 12 d^2 (the mean of J++, J+x, Jx+ without its scale)
+template <typename T>
+__device__ __forceinline__ T arakawa12(const St9<T>& a, const St9<T>& b) {
+  T jpp = (a.e - a.w) * (b.n - b.s) - (a.n - a.s) * (b.e - b.w);
+  T jpx = a.e * (b.ne - b.se) - a.w * (b.nw - b.sw) - a.n * (b.ne - b.nw) + a.s * (b.se - b.sw);
+  T jxp = b.n * (a.ne - a.nw) - b.s * (a.se - a.sw) - b.e * (a.ne - a.se) + b.w * (a.nw - a.sw);
+  return jpp + jpx + jxp;
+}
+
+template <typename T>
+__device__ __forceinline__ T lap5(const St9<T>& a) {
+  return a.e + a.w + a.n + a.s - (T)4 * a.c;
+}
+
+__constant__ double kBveA[3] = {0.5, 0.5, 1.0};
+__constant__ double kBveB[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+
+struct StencilConsts {
+  double c12;    // 1 / (12 d^2)
+  double nudd;   // nu / d^2
+  double famp;   // forcing amplitude
+  double fk_d;   // forcing wavenumber * d
+};
+
+// FWD stage: f = -J_A(psi, X_s) + nu Lap X_s + F; acc += b_s f; next = x + h a_s f
+// (s = 3: x += h acc). Single field.
+template <typename T>
+__global__ void bve_fwd_stage_kernel(int N, StencilConsts sc, int s, T h, const T* __restrict__ X,
+                                     const T* __restrict__ psi, T* acc, T* x, T* next) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= N || j >= N) return;
+  St9<T> q = ld9(X, N, i, j), ps = ld9(psi, N, i, j);
+  T f = -(T)sc.c12 * arakawa12(ps, q) + (T)sc.nudd * lap5(q) + (T)(sc.famp * sin(sc.fk_d * j));
+  size_t g = (size_t)j * N + i;
+  T a = (s == 0 ? (T)0 : acc[g]) + (T)kBveB[s] * f;
+  if (s < 3) {
+    acc[g] = a;
+    next[g] = x[g] + h * (T)kBveA[s] * f;
+  } else {
+    x[g] = x[g] + h * a;
+  }
+}
+
+// TLM stage over k directions (base q_s, psi_s shared)
+template <typename T>
+__global__ void bve_tlm_stage_kernel(int N, StencilConsts sc, int s, T h, const T* __restrict__ qb,
+                                     const T* __restrict__ pb, const T* __restrict__ cur,
+                                     const T* __restrict__ dpsi, T* acc, T* dx, T* next, size_t ld) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= N || j >= N) return;
+  const size_t off = (size_t)blockIdx.z * ld;
+  St9<T> q = ld9(qb, N, i, j), ps = ld9(pb, N, i, j);
+  St9<T> d = ld9(cur + off, N, i, j), dp = ld9(dpsi + off, N, i, j);
+  T dk = -(T)sc.c12 * (arakawa12(dp, q) + arakawa12(ps, d)) + (T)sc.nudd * lap5(d);
+  size_t g = off + (size_t)j * N + i;
+  T a = (s == 0 ? (T)0 : acc[g]) + (T)kBveB[s] * dk;
+  if (s < 3) {
+    acc[g] = a;
+    next[g] = dx[g] + h * (T)kBveA[s] * dk;
+  } else {
+    dx[g] = dx[g] + h * a;
+  }
+}
+
+// ADJ: T1 = J_A(q_s, kappa)
+template <typename T>
+__global__ void bve_adj_jac_kernel(int N, StencilConsts sc, const T* __restrict__ qb,
+                                   const T* __restrict__ kap, T* t1, size_t ld) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= N || j >= N) return;
+  const size_t off = (size_t)blockIdx.z * ld;
+  St9<T> q = ld9(qb, N, i, j), kk = ld9(kap + off, N, i, j);
+  t1[off + (size_t)j * N + i] = (T)sc.c12 * arakawa12(q, kk);
+}
+
+// ADJ stage: theta = -T2 + J_A(psi_s, kappa) + nu Lap kappa; th += theta;
+// s > 0: kappa_{s-1} = h b_{s-1} lam + h a_{s-1} theta; s = 0: lam += th
+template <typename T>
+__global__ void bve_adj_stage_kernel(int N, StencilConsts sc, int s, T h, const T* __restrict__ pb,
+                                     const T* __restrict__ kap, const T* __restrict__ t2, T* th,
+                                     T* lam, T* knext, size_t ld) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= N || j >= N) return;
+  const size_t off = (size_t)blockIdx.z * ld;
+  St9<T> ps = ld9(pb, N, i, j), kk = ld9(kap + off, N, i, j);
+  size_t g = off + (size_t)j * N + i;
+  T theta = -t2[g] + (T)sc.c12 * arakawa12(ps, kk) + (T)sc.nudd * lap5(kk);
+  T a = (s == 3 ? (T)0 : th[g]) + theta;
+  if (s > 0) {
+    th[g] = a;
+    knext[g] = h * (T)kBveB[s - 1] * lam[g] + h * (T)kBveA[s - 1] * theta;
+  } else {
+    lam[g] = lam[g] + a;
+  }
+}
+
+template <typename T>
+__global__ void scale_fields_kernel(size_t total, T a, const T* __restrict__ x, T* y) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x)
+    y[idx] = a * x[idx];
+}
+
+template <typename T>
+__global__ void copy_fields_kernel(size_t total, const T* __restrict__ x, T* y) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x)
+    y[idx] = x[idx];
+}
+
+// observation gather / scatter for k directions
+template <typename T>
+__global__ void bve_gather_kernel(int n_o, const int* __restrict__ sites, const T* __restrict__ X,
+                                  size_t ldx, T* W, int ldw, int row0, T inv_sigma) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  int col = blockIdx.y;
+  if (o < n_o) W[(size_t)col * ldw + row0 + o] = X[(size_t)col * ldx + sites[o]] * inv_sigma;
+}
+
+template <typename T>
+__global__ void bve_scatter_kernel(int n_o, const int* __restrict__ sites, const T* __restrict__ W,
+                                   int ldw, int row0, T* X, size_t ldx, T inv_sigma) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  int col = blockIdx.y;
+  if (o < n_o) atomicAdd(&X[(size_t)col * ldx + sites[o]], W[(size_t)col * ldw + row0 + o] * inv_sigma);
+}
+
+// FWD observation: obs_out = x[sites], d = (x[sites] - y) / sigma
+__global__ void bve_fwd_obs_kernel(int n_o, const int* __restrict__ sites, const double* __restrict__ x,
+                                   int row0, const double* __restrict__ y, double* d_out,
+                                   double* obs_out, double inv_sigma) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < n_o) {
+    double v = x[sites[o]];
+    if (obs_out) obs_out[row0 + o] = v;
+    if (d_out) d_out[row0 + o] = (v - y[row0 + o]) * inv_sigma;
+  }
+}
+
+// ------------------------------------------------------------------ host
+static int log2i(int n) { return 31 - __builtin_clz((unsigned)n); }
+
+template <typename C>
+static const C* tw_of(const BveGeom& g);
+template <> const double2* tw_of<double2>(const BveGeom& g) { return g.tw64; }
+template <> const float2* tw_of<float2>(const BveGeom& g) { return g.tw32; }
+
+template <typename R, typename RI, typename RO, typename RZ>
+int fft2_apply(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, const RZ* Z, int ldz,
+               const double* table, void* cbuf, cudaStream_t st) {
+  using C = typename CplxT<R>::C;
+  if (k <= 0) return SC4DVAR_OK;
+  const int N = g.N, logN = log2i(N);
+  const int pairs = (k + 1) / 2;
+  C* cb = reinterpret_cast<C*>(cbuf);
+  int RB = std::max(1, std::min(16, (int)(32768 / (N * sizeof(C)))));
+  while (N % RB) RB /= 2;
+  int CB = (sizeof(C) == 8 || N <= 512) ? 16 : 8;
+  size_t smr = (size_t)RB * N * sizeof(C);
+  size_t smc = (size_t)N * (CB + 1) * sizeof(C);
+  auto kr = fft2_rows_fwd<C, RI>;
+  auto kc = fft2_cols<C>;
+  auto ki = fft2_rows_inv<C, RO, RZ>;
+  SC4_CUDA(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+  SC4_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+  SC4_CUDA(cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+  kr<<<dim3(N / RB, pairs), 256, smr, st>>>(N, logN, k, X, ldx, cb, tw_of<C>(g), RB);
+  SC4_LAUNCH_CHECK();
+  kc<<<dim3(N / CB, pairs), 256, smc, st>>>(N, logN, cb, table, tw_of<C>(g), CB);
+  SC4_LAUNCH_CHECK();
+  ki<<<dim3(N / RB, pairs), 256, smr, st>>>(N, logN, k, cb, Y, ldy, Z, ldz, tw_of<C>(g), RB);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+int bve_setup(BveGeom& g, cudaStream_t st) {
+  const int N = g.N;
+  bve_twiddle_kernel<<<div_up(N / 2, 256), 256, 0, st>>>(N, g.tw64, g.tw32);
+  SC4_LAUNCH_CHECK();
+  size_t nn = (size_t)N * N;
+  bve_table_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(N, 0, 0.0, 0.0, g.poisson);
+  SC4_LAUNCH_CHECK();
+  bve_table_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(N, 1, g.prior_c, g.prior_ell, g.prior);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+static StencilConsts consts(const BveGeom& g) {
+  double d = 2.0 * M_PI / g.N;
+  StencilConsts c;
+  c.c12 = 1.0 / (12.0 * d * d);
+  c.nudd = g.nu / (d * d);
+  c.famp = g.famp;
+  c.fk_d = g.fk * d;
+  return c;
+}
+
+static dim3 sgrid(int N, int k) { return dim3(div_up(N, 32), div_up(N, 8), k); }
+
+template <typename T>
+static int scale_fields(size_t total, T a, const T* x, T* y, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>((total + 255) / 256, 8 * 152);
+  scale_fields_kernel<T><<<blocks, 256, 0, st>>>(total, a, x, y);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+template <typename T>
+static int copy_fields(size_t total, const T* x, T* y, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>((total + 255) / 256, 8 * 152);
+  copy_fields_kernel<T><<<blocks, 256, 0, st>>>(total, x, y);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+__global__ void bve_d2f_kernel(size_t total, const double* __restrict__ x, float* y) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x)
+    y[idx] = (float)x[idx];
+}
+
+static int d2f(size_t total, const double* x, float* y, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>((total + 255) / 256, 8 * 152);
+  bve_d2f_kernel<<<blocks, 256, 0, st>>>(total, x, y);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+// FWD in FP64 from x0. When q64/p64 are given, stores the stage states q_s(t),
+// psi_s(t) at row 4 t + s (and FP32 copies when q32/p32 are given); writes the
+// observation outputs. ws: bve_fwd_ws_bytes.
+int bve_fwd(const BveGeom& g, const double* x0, double* q64, double* p64, float* q32, float* p32,
+            const double* y, double* d_out, double* obs_out, double* xN, void* ws, cudaStream_t st) {
+  const int N = g.N;
+  const size_t n = (size_t)N * N;
+  double* x = reinterpret_cast<double*>(ws);
+  double* acc = x + n;
+  double* S[2] = {acc + n, acc + 2 * n};
+  double* ptmp = acc + 3 * n;
+  void* cbuf = ptmp + n;
+  StencilConsts sc = consts(g);
+  SC4_TRY(copy_fields<double>(n, x0, x, st));
+  const dim3 grid = sgrid(N, 1), blk(32, 8);
+  for (int t = 0;; ++t) {
+    int oi = g.obs_of_step_h[t];
+    if (oi >= 0 && (d_out || obs_out)) {
+      bve_fwd_obs_kernel<<<div_up(g.n_o, 256), 256, 0, st>>>(g.n_o, g.obs_idx + (size_t)oi * g.n_o, x,
+                                                             oi * g.n_o, y, d_out, obs_out,
+                                                             1.0 / g.sigma);
+      SC4_LAUNCH_CHECK();
+    }
+    if (t == g.Nsteps) break;
+    for (int s = 0; s < 4; ++s) {
+      const double* Xs = (s == 0) ? x : S[(s - 1) & 1];
+      double* nxt = (s < 3) ? S[s & 1] : nullptr;
+      size_t row = (size_t)(4 * t + s) * n;
+      double* ps = p64 ? p64 + row : ptmp;
+      SC4_TRY(fft2_apply<double, double, double, double>(g, 1, Xs, (int)n, ps, (int)n,
+                                                         (const double*)nullptr, 0, g.poisson, cbuf, st));
+      if (q64) SC4_TRY(copy_fields<double>(n, Xs, q64 + row, st));
+      if (q32) {
+        SC4_TRY(d2f(n, Xs, q32 + row, st));
+        SC4_TRY(d2f(n, ps, p32 + row, st));
+      }
+      bve_fwd_stage_kernel<double><<<grid, blk, 0, st>>>(N, sc, s, g.h, Xs, ps, acc, x, nxt);
+      SC4_LAUNCH_CHECK();
+    }
+  }
+  if (xN) SC4_TRY(copy_fields<double>(n, x, xN, st));
+  return SC4DVAR_OK;
+}
+
+template <typename T>
+static const T* qbase(const BveGeom& g);
+template <> const double* qbase<double>(const BveGeom& g) { return g.q64; }
+template <> const float* qbase<float>(const BveGeom& g) { return g.q32; }
+template <typename T>
+static const T* pbase(const BveGeom& g);
+template <> const double* pbase<double>(const BveGeom& g) { return g.p64; }
+template <> const float* pbase<float>(const BveGeom& g) { return g.p32; }
+
+// TLM of k directions: W = R^{-1/2} O_i dx_{t_i}; U0 = initial dx (n x k, ld ldu).
+// ws: bve_sweep_ws_bytes (five n k fields of T, then the complex FFT buffer).
+template <typename T>
+int bve_tlm(const BveGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* ws, cudaStream_t st) {
+  if (k <= 0) return SC4DVAR_OK;
+  const int N = g.N;
+  const size_t n = (size_t)N * N, nk = n * k;
+  T* dx = reinterpret_cast<T*>(ws);
+  T* acc = dx + nk;
+  T* S[2] = {acc + nk, acc + 2 * nk};
+  T* dpsi = acc + 3 * nk;
+  void* cbuf = dpsi + nk;
+  StencilConsts sc = consts(g);
+  const T inv_sigma = (T)(1.0 / g.sigma);
+  for (int c = 0; c < k; ++c)
+    SC4_CUDA(cudaMemcpyAsync(dx + (size_t)c * n, U0 + (size_t)c * ldu, n * sizeof(T),
+                             cudaMemcpyDeviceToDevice, st));
+  const dim3 grid = sgrid(N, k), blk(32, 8);
+  for (int t = 0;; ++t) {
+    int oi = g.obs_of_step_h[t];
+    if (oi >= 0) {
+      bve_gather_kernel<T><<<dim3(div_up(g.n_o, 256), k), 256, 0, st>>>(
+          g.n_o, g.obs_idx + (size_t)oi * g.n_o, dx, n, W, ldw, oi * g.n_o, inv_sigma);
+      SC4_LAUNCH_CHECK();
+    }
+    if (t == g.Nsteps) break;
+    for (int s = 0; s < 4; ++s) {
+      const T* cur = (s == 0) ? dx : S[(s - 1) & 1];
+      T* nxt = (s < 3) ? S[s & 1] : nullptr;
+      size_t row = (size_t)(4 * t + s) * n;
+      SC4_TRY(fft2_apply<T, T, T, T>(g, k, cur, (int)n, dpsi, (int)n, (const T*)nullptr, 0, g.poisson,
+                                     cbuf, st));
+      bve_tlm_stage_kernel<T><<<grid, blk, 0, st>>>(N, sc, s, (T)g.h, qbase<T>(g) + row,
+                                                    pbase<T>(g) + row, cur, dpsi, acc, dx, nxt, n);
+      SC4_LAUNCH_CHECK();
+    }
+  }
+  return SC4DVAR_OK;
+}
+
+// ADJ of k directions: Out = lam_0 forced by W. ws as for bve_tlm.
+template <typename T>
+int bve_adj(const BveGeom& g, const T* W, int ldw, int k, T* Out, int ldo, void* ws, cudaStream_t st) {
+  if (k <= 0) return SC4DVAR_OK;
+  const int N = g.N;
+  const size_t n = (size_t)N * N, nk = n * k;
+  T* lam = reinterpret_cast<T*>(ws);
+  T* th = lam + nk;
+  T* K[2] = {th + nk, th + 2 * nk};
+  T* t12 = th + 3 * nk;
+  void* cbuf = t12 + nk;
+  StencilConsts sc = consts(g);
+  const T inv_sigma = (T)(1.0 / g.sigma);
+  SC4_CUDA(cudaMemsetAsync(lam, 0, nk * sizeof(T), st));
+  const dim3 grid = sgrid(N, k), blk(32, 8);
+  const T h = (T)g.h;
+  for (int t = g.Nsteps; t >= 1; --t) {
+    int oi = g.obs_of_step_h[t];
+    if (oi >= 0) {
+      bve_scatter_kernel<T><<<dim3(div_up(g.n_o, 256), k), 256, 0, st>>>(
+          g.n_o, g.obs_idx + (size_t)oi * g.n_o, W, ldw, oi * g.n_o, lam, n, inv_sigma);
+      SC4_LAUNCH_CHECK();
+    }
+    SC4_TRY(scale_fields<T>(nk, h * (T)(1.0 / 6.0), lam, K[0], st));  // kappa_4 = h b_4 lam
+    for (int s = 3; s >= 0; --s) {
+      const T* kap = K[(3 - s) & 1];
+      T* knext = K[(4 - s) & 1];
+      size_t row = (size_t)(4 * (t - 1) + s) * n;
+      bve_adj_jac_kernel<T><<<grid, blk, 0, st>>>(N, sc, qbase<T>(g) + row, kap, t12, n);
+      SC4_LAUNCH_CHECK();
+      SC4_TRY(fft2_apply<T, T, T, T>(g, k, t12, (int)n, t12, (int)n, (const T*)nullptr, 0, g.poisson,
+                                     cbuf, st));
+      bve_adj_stage_kernel<T><<<grid, blk, 0, st>>>(N, sc, s, h, pbase<T>(g) + row, kap, t12, th, lam,
+                                                    s > 0 ? knext : nullptr, n);
+      SC4_LAUNCH_CHECK();
+    }
+  }
+  for (int c = 0; c < k; ++c)
+    SC4_CUDA(cudaMemcpyAsync(Out + (size_t)c * ldo, lam + (size_t)c * n, n * sizeof(T),
+                             cudaMemcpyDeviceToDevice, st));
+  return SC4DVAR_OK;
+}
+
+// Workspace of bve_tlm / bve_adj: five n x k fields of T (TLM: dx, acc, two
+// stage buffers, dpsi; ADJ: lam, th, two kappa buffers, T1/T2) followed by the
+// complex FFT buffer of ceil(k/2) n complex values.
+size_t bve_sweep_ws_bytes(const BveGeom& g, int k, size_t tb) {
+  size_t n = (size_t)g.N * g.N;
+  return 5 * n * k * tb + (size_t)((k + 1) / 2) * n * 2 * tb + 256;
+}
+
+size_t bve_fwd_ws_bytes(const BveGeom& g) {
+  size_t n = (size_t)g.N * g.N;
+  return 5 * n * sizeof(double) + n * sizeof(double2) + 256;
+}
+
+template int fft2_apply<double, double, double, double>(const BveGeom&, int, const double*, int, double*,
+                                                        int, const double*, int, const double*, void*,
+                                                        cudaStream_t);
+template int fft2_apply<float, float, float, float>(const BveGeom&, int, const float*, int, float*, int,
+                                                    const float*, int, const double*, void*,
+                                                    cudaStream_t);
+template int fft2_apply<double, double, float, float>(const BveGeom&, int, const double*, int, float*,
+                                                      int, const float*, int, const double*, void*,
+                                                      cudaStream_t);
+template int fft2_apply<double, float, double, double>(const BveGeom&, int, const float*, int, double*,
+                                                       int, const double*, int, const double*, void*,
+                                                       cudaStream_t);
+template int bve_tlm<double>(const BveGeom&, const double*, int, int, double*, int, void*, cudaStream_t);
+template int bve_tlm<float>(const BveGeom&, const float*, int, int, float*, int, void*, cudaStream_t);
+template int bve_adj<double>(const BveGeom&, const double*, int, int, double*, int, void*, cudaStream_t);
+template int bve_adj<float>(const BveGeom&, const float*, int, int, float*, int, void*, cudaStream_t);
+
+}  // namespace sc4

@@ -1,0 +1,39 @@
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace sc4 {
+
+// Geometry and device tables of a barotropic vorticity problem.
+struct BveGeom {
+  int N;                     // grid points per side (power of two)
+  int Nsteps;                // RK4 steps
+  int n_t, n_o;
+  double h, nu, sigma, famp, prior_c, prior_ell;
+  int fk;
+  const int* obs_of_step_h;  // host [Nsteps+1]
+  const int* obs_idx;        // device [n_t * n_o]
+  double2* tw64;             // device [N/2] twiddles
+  float2* tw32;
+  double* poisson;           // device [N*N] symbol -1/|kappa|^2
+  double* prior;             // device [N*N] symbol of Gamma^{1/2}
+  const double* q64;         // stored stage states, row 4 t + s
+  const double* p64;
+  const float* q32;
+  const float* p32;
+};
+
+int bve_setup(BveGeom& g, cudaStream_t st);
+template <typename R, typename RI, typename RO, typename RZ>
+int fft2_apply(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, const RZ* Z, int ldz,
+               const double* table, void* cbuf, cudaStream_t st);
+int bve_fwd(const BveGeom& g, const double* x0, double* q64, double* p64, float* q32, float* p32,
+            const double* y, double* d_out, double* obs_out, double* xN, void* ws, cudaStream_t st);
+template <typename T>
+int bve_tlm(const BveGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* ws, cudaStream_t st);
+template <typename T>
+int bve_adj(const BveGeom& g, const T* W, int ldw, int k, T* Out, int ldo, void* ws, cudaStream_t st);
+size_t bve_sweep_ws_bytes(const BveGeom& g, int k, size_t tb);
+size_t bve_fwd_ws_bytes(const BveGeom& g);
+
+}  // namespace sc4

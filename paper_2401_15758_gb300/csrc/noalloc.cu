@@ -116,6 +116,7 @@ extern "C" int sc4dvar_gn_hessian_apply_block_noalloc(sc4dvar_problem_t P, const
     set_error("no forward trajectory (call sc4dvar_fwd first)");
     return SC4DVAR_ERR_STATE;
   }
+  SC4_ARG(P->model == SC4DVAR_MODEL_BURGERS1D, "the allocation-free product covers the Burgers model");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (prec == SC4DVAR_FP64)
     return hvp_noalloc<double>(P, (const double*)X, ldx, k, (double*)Y, ldy, misfit_only, st);

@@ -4,6 +4,8 @@
 #include <string>
 #include "common.cuh"
 #include "model.cuh"
+#include "bve.cuh"
+#include <vector>
 
 namespace sc4 {
 
@@ -49,6 +51,15 @@ struct sc4dvar_problem_s {
   double* traj64 = nullptr;
   float* traj32 = nullptr;
   bool have_traj = false;
+  // barotropic vorticity problems: geometry, tables and stored stage states
+  sc4::BveGeom bve{};
+  std::vector<int> obs_of_step_h;
+  double2* bve_tw64 = nullptr;
+  float2* bve_tw32 = nullptr;
+  double *bve_poisson = nullptr, *bve_prior = nullptr;
+  double *bve_q64 = nullptr, *bve_p64 = nullptr;
+  float *bve_q32 = nullptr, *bve_p32 = nullptr;
+  sc4::Buf wBve, wCplx;
   // scratch: block operator work arrays, reductions, small host-visible scalars
   sc4::Buf wU, wW, wL, part, scal, vec;
   int count_mode = sc4::kOnline;
