@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-gn-step", action="store_true", help="skip the time-to-solution part")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256"],
+                    help="the Burgers block (default) or the barotropic vorticity block")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
     return ap.parse_args()
@@ -193,6 +195,79 @@ def setup_problem(torch, dev):
     v0 = torch.zeros(wl.n, dtype=torch.float64, device=dev)
     J0 = prob.fwd(v0)
     return g, si, wl, prob, J0
+
+
+# Barotropic vorticity block (HBM-bound streaming sweeps). Algorithmic bytes
+# per Hessian product per grid point per RK4 step (FP32, 4 B values), counted
+# from the kernels: per TLM stage a 2D FFT multiplier on one field (6 field
+# passes: real in, complex out/in/out/in, real out) plus the stencil stage (6
+# field passes); per ADJ stage one Jacobian pass (2), the multiplier (6) and
+# the stage kernel (6): 4 x (12 + 14) = 104 field passes per step.
+BVE_PASSES_PER_STEP = 104
+BVE_K = 256
+
+
+def bve_arm(args):
+    import torch
+    import paper_2401_15758_gb300 as g
+    import sc4dvar_inputs as si
+    dev = torch.device("cuda", 0)
+    wl = si.bve_workload("bve_n256")
+    d = si.bve_draws(wl)
+    prob = g.Problem.from_bve_workload(wl, d)
+    xt = torch.tensor(d["x_true0"], device=dev)
+    obs, _ = prob.forecast(xt)
+    prob.set_observations(obs + d["sigma_obs"] * torch.tensor(d["xi_o"].reshape(-1), device=dev))
+    prob.set_background(xt + prob.prior_sqrt_apply(torch.tensor(d["xi_b"], device=dev)))
+    prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device=dev))
+    k = BVE_K
+    X = torch.tensor(si.gaussian_matrix(wl.seed, k, wl.n, stream=23), device=dev, dtype=torch.float32)
+    Y = torch.empty_like(X)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.zero_()
+        prob.gn_hessian_apply_block(X, prec=g.FP32, out=Y)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = g.lib.sc4dvar_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        prob.gn_hessian_apply_block(X, prec=g.FP32, out=Y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    launches = g.lib.sc4dvar_launch_count() - l0
+    clk = clocks.stop()
+    t = statistics.mean(ms) / 1e3
+    nbytes = BVE_PASSES_PER_STEP * wl.n * 4 * wl.n_steps * k
+    peak = measured_hbm_gbs()
+    out = {"metric": METRIC, "value": k / t, "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"bve_n256: doubly periodic barotropic vorticity {wl.N}x{wl.N}, "
+                                  f"{wl.n_steps} RK4 steps, m={wl.m}, block k={k}, FP32 sweeps",
+                      "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": k,
+                      "l2": "256 MiB write before every timed step"},
+           "roofline": {"bound": "hbm", "kernel": "block Hessian product (all sweep kernels)",
+                        "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": nbytes / t / 1e9 / peak, "traffic": None,
+                        "algorithmic_bytes": nbytes},
+           "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def gpu_arm(args):
@@ -384,13 +459,37 @@ def profile_case():
     print("profile case done")
 
 
+def profile_case_bve():
+    """One FP32 TLM block and one FP32 ADJ block (k = 256) of the 256 x 256
+    vorticity workload on its first 20 RK4 steps (two observation times)."""
+    import torch
+    import paper_2401_15758_gb300 as g
+    import sc4dvar_inputs as si
+    wl = si.bve_workload("bve_n256", n_steps=20)
+    d = si.bve_draws(wl)
+    prob = g.Problem.from_bve_workload(wl, d)
+    prob.set_background(torch.tensor(d["x_true0"], device="cuda"))
+    prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
+    X = torch.tensor(si.gaussian_matrix(wl.seed, BVE_K, wl.n, stream=23), device="cuda",
+                     dtype=torch.float32)
+    W = prob.tlm_block(X, prec=g.FP32)
+    prob.adj_block(W, prec=g.FP32)
+    torch.cuda.synchronize()
+    print("bve profile case done")
+
+
 def main():
     args = parse()
     if args.profile:
-        profile_case()
+        if args.workload == "bve_n256":
+            profile_case_bve()
+        else:
+            profile_case()
         return
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "bve_n256":
+        bve_arm(args)
     else:
         gpu_arm(args)
 

@@ -933,6 +933,8 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
         cudaMalloc(&P->bve_tw32, (Ng / 2) * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&P->bve_poisson, (size_t)n * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&P->bve_prior, (size_t)n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P->bve_tabc64, 2 * (size_t)n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P->bve_tabc32, 2 * (size_t)n * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&P->bve_q64, stages * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&P->bve_p64, stages * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&P->bve_q32, stages * sizeof(float)) != cudaSuccess ||
@@ -996,6 +998,10 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
     b.tw32 = P->bve_tw32;
     b.poisson = P->bve_poisson;
     b.prior = P->bve_prior;
+    b.poisson_c64 = P->bve_tabc64;
+    b.prior_c64 = P->bve_tabc64 + n;
+    b.poisson_c32 = P->bve_tabc32;
+    b.prior_c32 = P->bve_tabc32 + n;
     b.q64 = P->bve_q64;
     b.p64 = P->bve_p64;
     b.q32 = P->bve_q32;
@@ -1029,6 +1035,7 @@ int sc4dvar_problem_destroy(sc4dvar_problem_t P) {
   cudaFree(P->xb); cudaFree(P->y); cudaFree(P->v); cudaFree(P->x0); cudaFree(P->d);
   cudaFree(P->traj64); cudaFree(P->traj32);
   cudaFree(P->bve_tw64); cudaFree(P->bve_tw32); cudaFree(P->bve_poisson); cudaFree(P->bve_prior);
+  cudaFree(P->bve_tabc64); cudaFree(P->bve_tabc32);
   cudaFree(P->bve_q64); cudaFree(P->bve_p64); cudaFree(P->bve_q32); cudaFree(P->bve_p32);
   P->wBve.release(); P->wCplx.release();
   P->wU.release(); P->wW.release(); P->wL.release(); P->part.release(); P->scal.release();

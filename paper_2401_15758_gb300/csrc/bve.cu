@@ -163,6 +163,175 @@ __global__ void fft2_rows_inv(int N, int logN, int k, const C* cbuf, RO* __restr
   }
 }
 
+// ---- warp-resident FFTs (N >= 32): lane l holds elements i = r * 32 + l ----
+// Stages whose butterfly span is below 32 exchange values across lanes with
+// shfl_xor; longer spans pair registers of the same lane. DIF: natural order in,
+// bit-reversed out. DIT: bit-reversed in, natural out. No shared memory and no
+// barriers; twiddles w_j = exp(-2 pi i j / N) from the table (conjugated for the
+// inverse).
+template <typename C>
+__device__ __forceinline__ C shfl_xor_c(C v, int m) {
+  C o;
+  o.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  o.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return o;
+}
+
+template <typename C>
+__device__ __forceinline__ C twid(const C* __restrict__ tw, int j, int dir) {
+  C w = __ldg(tw + j);
+  if (dir > 0) w.y = -w.y;
+  return w;
+}
+
+template <typename C, int R>
+__device__ __forceinline__ void warp_fft_dif(C (&v)[R], int lane, const C* __restrict__ tw, int N, int dir) {
+#pragma unroll
+  for (int hr = R / 2; hr >= 1; hr >>= 1) {
+    const int stride = N / (64 * hr);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & hr) continue;
+      C u = v[r], x = v[r + hr];
+      C w = twid(tw, ((r % hr) * 32 + lane) * stride, dir);
+      v[r] = cmk<C>(u.x + x.x, u.y + x.y);
+      v[r + hr] = cmulc(w, cmk<C>(u.x - x.x, u.y - x.y));
+    }
+  }
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool upper = (lane & half) == 0;
+    C w = twid(tw, (lane & (half - 1)) * (N / (2 * half)), dir);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      C o = shfl_xor_c(v[r], half);
+      if (upper) v[r] = cmk<C>(v[r].x + o.x, v[r].y + o.y);
+      else v[r] = cmulc(w, cmk<C>(o.x - v[r].x, o.y - v[r].y));
+    }
+  }
+}
+
+template <typename C, int R>
+__device__ __forceinline__ void warp_fft_dit(C (&v)[R], int lane, const C* __restrict__ tw, int N, int dir) {
+#pragma unroll
+  for (int half = 1; half <= 16; half <<= 1) {
+    const bool upper = (lane & half) == 0;
+    C w = twid(tw, (lane & (half - 1)) * (N / (2 * half)), dir);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      C o = shfl_xor_c(v[r], half);
+      if (upper) {
+        C t = cmulc(w, o);
+        v[r] = cmk<C>(v[r].x + t.x, v[r].y + t.y);
+      } else {
+        C t = cmulc(w, v[r]);
+        v[r] = cmk<C>(o.x - t.x, o.y - t.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int hr = 1; hr < R; hr <<= 1) {
+    const int stride = N / (64 * hr);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & hr) continue;
+      C w = twid(tw, ((r % hr) * 32 + lane) * stride, dir);
+      C t = cmulc(w, v[r + hr]);
+      v[r + hr] = cmk<C>(v[r].x - t.x, v[r].y - t.y);
+      v[r] = cmk<C>(v[r].x + t.x, v[r].y + t.y);
+    }
+  }
+}
+
+// rows forward: one warp per row of a field pair; complex output in bit-reversed kx order
+template <typename C, typename RI, int R>
+__global__ void __launch_bounds__(256) wfft_rows_fwd(int N, int k, const RI* __restrict__ X, int ldx,
+                                                     C* cbuf, const C* __restrict__ tw) {
+  using Rl = typename CplxOf<C>::R;
+  const int lane = threadIdx.x & 31, j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int p = blockIdx.y, fa = 2 * p, fb = 2 * p + 1;
+  if (j >= N) return;
+  const bool hasb = fb < k;
+  const RI* xa = X + (size_t)fa * ldx + (size_t)j * N;
+  const RI* xb = X + (size_t)fb * ldx + (size_t)j * N;
+  C v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = cmk<C>((Rl)xa[r * 32 + lane], hasb ? (Rl)xb[r * 32 + lane] : (Rl)0);
+  warp_fft_dif<C, R>(v, lane, tw, N, -1);
+  C* out = cbuf + (size_t)p * N * N + (size_t)j * N;
+#pragma unroll
+  for (int r = 0; r < R; ++r) out[r * 32 + lane] = v[r];
+}
+
+// columns: forward along y (DIF), symbol at bit-reversed (ky, kx), inverse (DIT)
+template <typename C, int R>
+__global__ void __launch_bounds__(256) wfft_cols(int N, int logN, C* cbuf,
+                                                 const typename CplxOf<C>::R* __restrict__ tcol,
+                                                 const C* __restrict__ tw, int CB) {
+  using Rl = typename CplxOf<C>::R;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tile = reinterpret_cast<C*>(smraw);  // [N][CB+1]
+  const int ld = CB + 1, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int p = blockIdx.y, i0 = blockIdx.x * CB;
+  C* g = cbuf + (size_t)p * N * N;
+  for (int it = threadIdx.x; it < N * CB; it += blockDim.x) {
+    int j = it / CB, c = it - j * CB;
+    tile[j * ld + c] = g[(size_t)j * N + i0 + c];
+  }
+  __syncthreads();
+  for (int c = wid; c < CB; c += 8) {
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = tile[(r * 32 + lane) * ld + c];
+    warp_fft_dif<C, R>(v, lane, tw, N, -1);
+    const Rl* tc = tcol + (size_t)(i0 + c) * N;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      Rl sv = __ldg(tc + r * 32 + lane);
+      v[r] = cmk<C>(v[r].x * sv, v[r].y * sv);
+    }
+    warp_fft_dit<C, R>(v, lane, tw, N, +1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) tile[(r * 32 + lane) * ld + c] = v[r];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < N * CB; it += blockDim.x) {
+    int j = it / CB, c = it - j * CB;
+    g[(size_t)j * N + i0 + c] = tile[j * ld + c];
+  }
+}
+
+// rows inverse: bit-reversed kx in (DIT), natural x out, scaled 1/N^2 (+ Z)
+template <typename C, typename RO, typename RZ, int R>
+__global__ void __launch_bounds__(256) wfft_rows_inv(int N, int k, const C* cbuf, RO* __restrict__ Y,
+                                                     int ldy, const RZ* __restrict__ Z, int ldz,
+                                                     const C* __restrict__ tw) {
+  using Rl = typename CplxOf<C>::R;
+  const int lane = threadIdx.x & 31, j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int p = blockIdx.y, fa = 2 * p, fb = 2 * p + 1;
+  if (j >= N) return;
+  const bool hasb = fb < k;
+  const C* in = cbuf + (size_t)p * N * N + (size_t)j * N;
+  C v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = in[r * 32 + lane];
+  warp_fft_dit<C, R>(v, lane, tw, N, +1);
+  const Rl scale = (Rl)1 / ((Rl)N * (Rl)N);
+  const size_t ra = (size_t)fa * ldy + (size_t)j * N, rb = (size_t)fb * ldy + (size_t)j * N;
+  const size_t za = (size_t)fa * ldz + (size_t)j * N, zb = (size_t)fb * ldz + (size_t)j * N;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = r * 32 + lane;
+    Rl a = v[r].x * scale, b = v[r].y * scale;
+    if (Z) {
+      a += (Rl)Z[za + i];
+      if (hasb) b += (Rl)Z[zb + i];
+    }
+    Y[ra + i] = (RO)a;
+    if (hasb) Y[rb + i] = (RO)b;
+  }
+}
+
 __global__ void bve_twiddle_kernel(int N, double2* tw64, float2* tw32) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < N / 2) {
@@ -170,6 +339,18 @@ __global__ void bve_twiddle_kernel(int N, double2* tw64, float2* tw32) {
     sincospi(-2.0 * (double)j / (double)N, &s, &c);
     tw64[j] = make_double2(c, s);
     tw32[j] = make_float2((float)c, (float)s);
+  }
+}
+
+// Column-kernel copy of a symbol table: entry (c, i) = S(ky = bitrev(i), kx =
+// bitrev(c)) at c * N + i, in the real type of the transform (the warp FFTs
+// leave both wavenumbers in bit-reversed order), so a lane's lookup is contiguous.
+template <typename R>
+__global__ void bve_table_cols_kernel(int N, int logN, const double* __restrict__ table, R* out) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx < (size_t)N * N) {
+    int c = (int)(idx / N), i = (int)(idx % N);
+    out[idx] = (R)table[(size_t)brev_n(i, logN) * N + brev_n(c, logN)];
   }
 }
 
@@ -191,19 +372,46 @@ struct St9 {
   T c, e, w, n, s, ne, nw, se, sw;
 };
 
+// Values (x_{i-1}, x_i, x_{i+1}) of row j of a periodic field.
 template <typename T>
-__device__ __forceinline__ St9<T> ld9(const T* __restrict__ f, int N, int i, int j) {
-  const int ip = (i + 1) & (N - 1), im = (i - 1) & (N - 1);
-  const int jp = (j + 1) & (N - 1), jm = (j - 1) & (N - 1);
-  St9<T> v;
-  const T* r0 = f + (size_t)j * N;
-  const T* rp = f + (size_t)jp * N;
-  const T* rm = f + (size_t)jm * N;
-  v.c = __ldg(r0 + i); v.e = __ldg(r0 + ip); v.w = __ldg(r0 + im);
-  v.n = __ldg(rp + i); v.s = __ldg(rm + i);
-  v.ne = __ldg(rp + ip); v.nw = __ldg(rp + im); v.se = __ldg(rm + ip); v.sw = __ldg(rm + im);
+struct Row3 {
+  T w, c, e;
+};
+
+template <typename T>
+__device__ __forceinline__ Row3<T> ld3(const T* __restrict__ f, int N, int i, int j) {
+  const T* r = f + (size_t)(j & (N - 1)) * N;
+  Row3<T> v;
+  v.w = __ldg(r + ((i - 1) & (N - 1)));
+  v.c = __ldg(r + i);
+  v.e = __ldg(r + ((i + 1) & (N - 1)));
   return v;
 }
+
+template <typename T>
+__device__ __forceinline__ St9<T> st9(const Row3<T>& s, const Row3<T>& m, const Row3<T>& n) {
+  St9<T> v;
+  v.c = m.c; v.e = m.e; v.w = m.w;
+  v.n = n.c; v.s = s.c; v.ne = n.e; v.nw = n.w; v.se = s.e; v.sw = s.w;
+  return v;
+}
+
+// A sliding three-row window over one field: rows j-1, j, j+1 in registers.
+template <typename T>
+struct Win {
+  Row3<T> s, m, n;
+  __device__ __forceinline__ void init(const T* f, int N, int i, int j) {
+    s = ld3(f, N, i, j - 1);
+    m = ld3(f, N, i, j);
+    n = ld3(f, N, i, j + 1);
+  }
+  __device__ __forceinline__ void advance(const T* f, int N, int i, int j) {  // j: new centre row
+    s = m;
+    m = n;
+    n = ld3(f, N, i, j + 1);
+  }
+  __device__ __forceinline__ St9<T> st() const { return st9(s, m, n); }
+};
 
 // Arakawa J_A(a, b) times 12 d^2 (the mean of J++, J+x, Jx+ without its scale)
 template <typename T>
@@ -229,75 +437,118 @@ struct StencilConsts {
   double fk_d;   // forcing wavenumber * d
 };
 
+// Stencil kernels: thread (x = i, rows j0 .. j0 + JB - 1) slides a three-row
+// window along y, so each field costs three loads per point instead of nine.
+
 // FWD stage: f = -J_A(psi, X_s) + nu Lap X_s + F; acc += b_s f; next = x + h a_s f
 // (s = 3: x += h acc). Single field.
 template <typename T>
-__global__ void bve_fwd_stage_kernel(int N, StencilConsts sc, int s, T h, const T* __restrict__ X,
+__global__ void bve_fwd_stage_kernel(int N, int JB, StencilConsts sc, int s, T h, const T* __restrict__ X,
                                      const T* __restrict__ psi, T* acc, T* x, T* next) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= N || j >= N) return;
-  St9<T> q = ld9(X, N, i, j), ps = ld9(psi, N, i, j);
-  T f = -(T)sc.c12 * arakawa12(ps, q) + (T)sc.nudd * lap5(q) + (T)(sc.famp * sin(sc.fk_d * j));
-  size_t g = (size_t)j * N + i;
-  T a = (s == 0 ? (T)0 : acc[g]) + (T)kBveB[s] * f;
-  if (s < 3) {
-    acc[g] = a;
-    next[g] = x[g] + h * (T)kBveA[s] * f;
-  } else {
-    x[g] = x[g] + h * a;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * JB;
+  if (i >= N || j0 >= N) return;
+  Win<T> q, ps;
+  q.init(X, N, i, j0);
+  ps.init(psi, N, i, j0);
+  for (int jj = 0; jj < JB; ++jj) {
+    const int j = j0 + jj;
+    if (jj) { q.advance(X, N, i, j); ps.advance(psi, N, i, j); }
+    St9<T> qq = q.st(), pp = ps.st();
+    T f = -(T)sc.c12 * arakawa12(pp, qq) + (T)sc.nudd * lap5(qq) + (T)(sc.famp * sin(sc.fk_d * j));
+    size_t g = (size_t)j * N + i;
+    T a = (s == 0 ? (T)0 : acc[g]) + (T)kBveB[s] * f;
+    if (s < 3) {
+      acc[g] = a;
+      next[g] = x[g] + h * (T)kBveA[s] * f;
+    } else {
+      x[g] = x[g] + h * a;
+    }
   }
 }
 
 // TLM stage over k directions (base q_s, psi_s shared)
 template <typename T>
-__global__ void bve_tlm_stage_kernel(int N, StencilConsts sc, int s, T h, const T* __restrict__ qb,
+__global__ void bve_tlm_stage_kernel(int N, int JB, StencilConsts sc, int s, T h, const T* __restrict__ qb,
                                      const T* __restrict__ pb, const T* __restrict__ cur,
                                      const T* __restrict__ dpsi, T* acc, T* dx, T* next, size_t ld) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= N || j >= N) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * JB;
+  if (i >= N || j0 >= N) return;
   const size_t off = (size_t)blockIdx.z * ld;
-  St9<T> q = ld9(qb, N, i, j), ps = ld9(pb, N, i, j);
-  St9<T> d = ld9(cur + off, N, i, j), dp = ld9(dpsi + off, N, i, j);
-  T dk = -(T)sc.c12 * (arakawa12(dp, q) + arakawa12(ps, d)) + (T)sc.nudd * lap5(d);
-  size_t g = off + (size_t)j * N + i;
-  T a = (s == 0 ? (T)0 : acc[g]) + (T)kBveB[s] * dk;
-  if (s < 3) {
-    acc[g] = a;
-    next[g] = dx[g] + h * (T)kBveA[s] * dk;
-  } else {
-    dx[g] = dx[g] + h * a;
+  const T* cu = cur + off;
+  const T* dp = dpsi + off;
+  Win<T> q, ps, d, dpw;
+  q.init(qb, N, i, j0);
+  ps.init(pb, N, i, j0);
+  d.init(cu, N, i, j0);
+  dpw.init(dp, N, i, j0);
+  const T bs = (T)kBveB[s];
+  const T ha = (s < 3) ? h * (T)kBveA[s] : (T)0;
+  for (int jj = 0; jj < JB; ++jj) {
+    const int j = j0 + jj;
+    if (jj) { q.advance(qb, N, i, j); ps.advance(pb, N, i, j); d.advance(cu, N, i, j); dpw.advance(dp, N, i, j); }
+    St9<T> qq = q.st(), pp = ps.st(), dd = d.st(), ddp = dpw.st();
+    T dk = -(T)sc.c12 * (arakawa12(ddp, qq) + arakawa12(pp, dd)) + (T)sc.nudd * lap5(dd);
+    size_t g = off + (size_t)j * N + i;
+    T a = (s == 0 ? (T)0 : acc[g]) + bs * dk;
+    if (s < 3) {
+      acc[g] = a;
+      next[g] = dx[g] + ha * dk;
+    } else {
+      dx[g] = dx[g] + h * a;
+    }
   }
 }
 
 // ADJ: T1 = J_A(q_s, kappa)
 template <typename T>
-__global__ void bve_adj_jac_kernel(int N, StencilConsts sc, const T* __restrict__ qb,
+__global__ void bve_adj_jac_kernel(int N, int JB, StencilConsts sc, const T* __restrict__ qb,
                                    const T* __restrict__ kap, T* t1, size_t ld) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= N || j >= N) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * JB;
+  if (i >= N || j0 >= N) return;
   const size_t off = (size_t)blockIdx.z * ld;
-  St9<T> q = ld9(qb, N, i, j), kk = ld9(kap + off, N, i, j);
-  t1[off + (size_t)j * N + i] = (T)sc.c12 * arakawa12(q, kk);
+  const T* kp = kap + off;
+  Win<T> q, kk;
+  q.init(qb, N, i, j0);
+  kk.init(kp, N, i, j0);
+  for (int jj = 0; jj < JB; ++jj) {
+    const int j = j0 + jj;
+    if (jj) { q.advance(qb, N, i, j); kk.advance(kp, N, i, j); }
+    t1[off + (size_t)j * N + i] = (T)sc.c12 * arakawa12(q.st(), kk.st());
+  }
 }
 
 // ADJ stage: theta = -T2 + J_A(psi_s, kappa) + nu Lap kappa; th += theta;
 // s > 0: kappa_{s-1} = h b_{s-1} lam + h a_{s-1} theta; s = 0: lam += th
 template <typename T>
-__global__ void bve_adj_stage_kernel(int N, StencilConsts sc, int s, T h, const T* __restrict__ pb,
+__global__ void bve_adj_stage_kernel(int N, int JB, StencilConsts sc, int s, T h, const T* __restrict__ pb,
                                      const T* __restrict__ kap, const T* __restrict__ t2, T* th,
                                      T* lam, T* knext, size_t ld) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= N || j >= N) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * JB;
+  if (i >= N || j0 >= N) return;
   const size_t off = (size_t)blockIdx.z * ld;
-  St9<T> ps = ld9(pb, N, i, j), kk = ld9(kap + off, N, i, j);
-  size_t g = off + (size_t)j * N + i;
-  T theta = -t2[g] + (T)sc.c12 * arakawa12(ps, kk) + (T)sc.nudd * lap5(kk);
-  T a = (s == 3 ? (T)0 : th[g]) + theta;
-  if (s > 0) {
-    th[g] = a;
-    knext[g] = h * (T)kBveB[s - 1] * lam[g] + h * (T)kBveA[s - 1] * theta;
-  } else {
-    lam[g] = lam[g] + a;
+  const T* kp = kap + off;
+  Win<T> ps, kk;
+  ps.init(pb, N, i, j0);
+  kk.init(kp, N, i, j0);
+  const T hb = (s > 0) ? h * (T)kBveB[s - 1] : (T)0;
+  const T ha = (s > 0) ? h * (T)kBveA[s - 1] : (T)0;
+  for (int jj = 0; jj < JB; ++jj) {
+    const int j = j0 + jj;
+    if (jj) { ps.advance(pb, N, i, j); kk.advance(kp, N, i, j); }
+    St9<T> k9 = kk.st();
+    size_t g = off + (size_t)j * N + i;
+    T theta = -t2[g] + (T)sc.c12 * arakawa12(ps.st(), k9) + (T)sc.nudd * lap5(k9);
+    T a = (s == 3 ? (T)0 : th[g]) + theta;
+    if (s > 0) {
+      th[g] = a;
+      knext[g] = hb * lam[g] + ha * theta;
+    } else {
+      lam[g] = lam[g] + a;
+    }
   }
 }
 
@@ -347,10 +598,38 @@ __global__ void bve_fwd_obs_kernel(int n_o, const int* __restrict__ sites, const
 // ------------------------------------------------------------------ host
 static int log2i(int n) { return 31 - __builtin_clz((unsigned)n); }
 
+// The column-ordered copy of `table` in the transform's real type.
+static const void* table_cols(const BveGeom& g, const double* table, size_t rb) {
+  if (table == g.poisson) return rb == 4 ? (const void*)g.poisson_c32 : (const void*)g.poisson_c64;
+  return rb == 4 ? (const void*)g.prior_c32 : (const void*)g.prior_c64;
+}
+
 template <typename C>
 static const C* tw_of(const BveGeom& g);
 template <> const double2* tw_of<double2>(const BveGeom& g) { return g.tw64; }
 template <> const float2* tw_of<float2>(const BveGeom& g) { return g.tw32; }
+
+
+
+template <typename C, typename RI, typename RO, typename RZ, int RR>
+static int wfft2(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, const RZ* Z, int ldz,
+                 const double* table, C* cb, cudaStream_t st) {
+  const int N = g.N, logN = log2i(N), pairs = (k + 1) / 2;
+  const int CB = (sizeof(C) == 8 || N <= 512) ? 16 : 8;
+  size_t smc = (size_t)N * (CB + 1) * sizeof(C);
+  auto kc = wfft_cols<C, RR>;
+  SC4_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+  wfft_rows_fwd<C, RI, RR><<<dim3(div_up(N, 8), pairs), 256, 0, st>>>(N, k, X, ldx, cb, tw_of<C>(g));
+  SC4_LAUNCH_CHECK();
+  using Rl = typename CplxOf<C>::R;
+  const Rl* tcol = reinterpret_cast<const Rl*>(table_cols(g, table, sizeof(Rl)));
+  kc<<<dim3(N / CB, pairs), 256, smc, st>>>(N, logN, cb, tcol, tw_of<C>(g), CB);
+  SC4_LAUNCH_CHECK();
+  wfft_rows_inv<C, RO, RZ, RR><<<dim3(div_up(N, 8), pairs), 256, 0, st>>>(N, k, cb, Y, ldy, Z, ldz,
+                                                                          tw_of<C>(g));
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
 
 template <typename R, typename RI, typename RO, typename RZ>
 int fft2_apply(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, const RZ* Z, int ldz,
@@ -360,6 +639,15 @@ int fft2_apply(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, co
   const int N = g.N, logN = log2i(N);
   const int pairs = (k + 1) / 2;
   C* cb = reinterpret_cast<C*>(cbuf);
+  switch (N) {
+    case 32: return wfft2<C, RI, RO, RZ, 1>(g, k, X, ldx, Y, ldy, Z, ldz, table, cb, st);
+    case 64: return wfft2<C, RI, RO, RZ, 2>(g, k, X, ldx, Y, ldy, Z, ldz, table, cb, st);
+    case 128: return wfft2<C, RI, RO, RZ, 4>(g, k, X, ldx, Y, ldy, Z, ldz, table, cb, st);
+    case 256: return wfft2<C, RI, RO, RZ, 8>(g, k, X, ldx, Y, ldy, Z, ldz, table, cb, st);
+    case 512: return wfft2<C, RI, RO, RZ, 16>(g, k, X, ldx, Y, ldy, Z, ldz, table, cb, st);
+    case 1024: return wfft2<C, RI, RO, RZ, 32>(g, k, X, ldx, Y, ldy, Z, ldz, table, cb, st);
+    default: break;  // N = 16: shared-memory radix-2 kernels below
+  }
   int RB = std::max(1, std::min(16, (int)(32768 / (N * sizeof(C)))));
   while (N % RB) RB /= 2;
   int CB = (sizeof(C) == 8 || N <= 512) ? 16 : 8;
@@ -389,6 +677,16 @@ int bve_setup(BveGeom& g, cudaStream_t st) {
   SC4_LAUNCH_CHECK();
   bve_table_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(N, 1, g.prior_c, g.prior_ell, g.prior);
   SC4_LAUNCH_CHECK();
+  const int logN = log2i(N);
+  const unsigned nb = (unsigned)((nn + 255) / 256);
+  bve_table_cols_kernel<double><<<nb, 256, 0, st>>>(N, logN, g.poisson, g.poisson_c64);
+  SC4_LAUNCH_CHECK();
+  bve_table_cols_kernel<float><<<nb, 256, 0, st>>>(N, logN, g.poisson, g.poisson_c32);
+  SC4_LAUNCH_CHECK();
+  bve_table_cols_kernel<double><<<nb, 256, 0, st>>>(N, logN, g.prior, g.prior_c64);
+  SC4_LAUNCH_CHECK();
+  bve_table_cols_kernel<float><<<nb, 256, 0, st>>>(N, logN, g.prior, g.prior_c32);
+  SC4_LAUNCH_CHECK();
   return SC4DVAR_OK;
 }
 
@@ -402,7 +700,10 @@ static StencilConsts consts(const BveGeom& g) {
   return c;
 }
 
-static dim3 sgrid(int N, int k) { return dim3(div_up(N, 32), div_up(N, 8), k); }
+// Rows per thread of the stencil kernels and the launch grid for k fields
+// (blocks of 32 x 8 threads, each thread JB rows).
+static int stencil_jb(int N) { return N >= 64 ? 8 : 2; }
+static dim3 sgrid(int N, int k) { return dim3(div_up(N, 32), div_up(N / stencil_jb(N), 8), k); }
 
 template <typename T>
 static int scale_fields(size_t total, T a, const T* x, T* y, cudaStream_t st) {
@@ -469,7 +770,7 @@ int bve_fwd(const BveGeom& g, const double* x0, double* q64, double* p64, float*
         SC4_TRY(d2f(n, Xs, q32 + row, st));
         SC4_TRY(d2f(n, ps, p32 + row, st));
       }
-      bve_fwd_stage_kernel<double><<<grid, blk, 0, st>>>(N, sc, s, g.h, Xs, ps, acc, x, nxt);
+      bve_fwd_stage_kernel<double><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, g.h, Xs, ps, acc, x, nxt);
       SC4_LAUNCH_CHECK();
     }
   }
@@ -518,7 +819,7 @@ int bve_tlm(const BveGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* 
       size_t row = (size_t)(4 * t + s) * n;
       SC4_TRY(fft2_apply<T, T, T, T>(g, k, cur, (int)n, dpsi, (int)n, (const T*)nullptr, 0, g.poisson,
                                      cbuf, st));
-      bve_tlm_stage_kernel<T><<<grid, blk, 0, st>>>(N, sc, s, (T)g.h, qbase<T>(g) + row,
+      bve_tlm_stage_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, (T)g.h, qbase<T>(g) + row,
                                                     pbase<T>(g) + row, cur, dpsi, acc, dx, nxt, n);
       SC4_LAUNCH_CHECK();
     }
@@ -554,11 +855,11 @@ int bve_adj(const BveGeom& g, const T* W, int ldw, int k, T* Out, int ldo, void*
       const T* kap = K[(3 - s) & 1];
       T* knext = K[(4 - s) & 1];
       size_t row = (size_t)(4 * (t - 1) + s) * n;
-      bve_adj_jac_kernel<T><<<grid, blk, 0, st>>>(N, sc, qbase<T>(g) + row, kap, t12, n);
+      bve_adj_jac_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, qbase<T>(g) + row, kap, t12, n);
       SC4_LAUNCH_CHECK();
       SC4_TRY(fft2_apply<T, T, T, T>(g, k, t12, (int)n, t12, (int)n, (const T*)nullptr, 0, g.poisson,
                                      cbuf, st));
-      bve_adj_stage_kernel<T><<<grid, blk, 0, st>>>(N, sc, s, h, pbase<T>(g) + row, kap, t12, th, lam,
+      bve_adj_stage_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, h, pbase<T>(g) + row, kap, t12, th, lam,
                                                     s > 0 ? knext : nullptr, n);
       SC4_LAUNCH_CHECK();
     }

@@ -57,6 +57,8 @@ struct sc4dvar_problem_s {
   double2* bve_tw64 = nullptr;
   float2* bve_tw32 = nullptr;
   double *bve_poisson = nullptr, *bve_prior = nullptr;
+  double* bve_tabc64 = nullptr;
+  float* bve_tabc32 = nullptr;
   double *bve_q64 = nullptr, *bve_p64 = nullptr;
   float *bve_q32 = nullptr, *bve_p32 = nullptr;
   sc4::Buf wBve, wCplx;
