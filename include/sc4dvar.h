@@ -278,6 +278,40 @@ int sc4dvar_sketchsolv(sc4dvar_precond_t P, const double* g_dev, double* dv_dev,
 int sc4dvar_gauss_newton(sc4dvar_problem_t p, const sc4dvar_gn_opts* opts, double* v_inout_dev,
                          sc4dvar_gn_info* info, void* stream);
 
+/* ---- batched serving ----------------------------------------------------------
+ * A batch of independent problems (any mix of grids, windows, observations and
+ * block widths). No counterpart in the paper: its experiments solve one problem
+ * at a time; serving many small problems at once is how a GPU is kept busy.
+ * sc4dvar_batch_hessian_apply: Y[b] = (I + A_b^T A_b) X[b] (or A_b^T A_b X[b]),
+ * X[b], Y[b] device blocks n_b x k[b] (ld n_b) in prec. The first call (and any
+ * call with other buffers, widths or flags) runs once eagerly to size the
+ * workspaces, then records all problems' kernels into one CUDA graph (problems
+ * on parallel branches); every later identical call is one graph launch.
+ * Problems must have a stored trajectory (sc4dvar_fwd); the graph stays valid
+ * across sc4dvar_fwd calls on the same handles. */
+typedef struct sc4dvar_batch_s* sc4dvar_batch_t;
+int sc4dvar_batch_create(const sc4dvar_problem_t* problems, int B, sc4dvar_batch_t* out);
+int sc4dvar_batch_destroy(sc4dvar_batch_t b);
+int sc4dvar_batch_hessian_apply(sc4dvar_batch_t b, const void* const* X_dev, void* const* Y_dev,
+                                const int* k, int misfit_only, int prec, void* stream);
+/* Batched PCG on (I + H_b) x_b = rhs_b (Eq. pcgsystem), x0 = 0, preconditioners
+ * P[b] (NULL entries or NULL array = none), operator arithmetic prec. _start
+ * initializes every problem and records one iteration of all problems into a
+ * CUDA graph; _step launches that graph nsteps times (scalars stay on the device;
+ * a problem whose |r| <= tol |rhs| or that broke down stops moving); _status
+ * reads relres, iterations and status (0 or SC4DVAR_ERR_BREAKDOWN) per problem;
+ * _solution copies the iterates out. */
+int sc4dvar_batch_pcg_start(sc4dvar_batch_t b, const sc4dvar_precond_t* P, const double* const* rhs_dev,
+                            double tol, int prec, void* stream);
+int sc4dvar_batch_pcg_step(sc4dvar_batch_t b, int nsteps, void* stream);
+int sc4dvar_batch_pcg_status(sc4dvar_batch_t b, double* relres_host, int* its_host, int* status_host,
+                             void* stream);
+int sc4dvar_batch_pcg_solution(sc4dvar_batch_t b, double* const* x_dev, void* stream);
+/* Times the packed FP32 sweep of a problem (n >= 1024) for each valid number of
+ * point pairs per thread with k directions and keeps the fastest for later
+ * sweeps; chosen (nullable) returns it (0: nothing to tune). Synchronizes. */
+int sc4dvar_autotune(sc4dvar_problem_t p, int k, int* chosen);
+
 int sc4dvar_counters(sc4dvar_problem_t p, sc4dvar_counters_t* out);
 int sc4dvar_counters_reset(sc4dvar_problem_t p);
 

@@ -280,6 +280,69 @@ class Problem:
         check(lib.sc4dvar_counters_reset(self.h))
 
 
+class Batch:
+    """Independent problems served together (graph-recorded batched operators)."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h for p in self.problems])
+        h = C.c_void_p()
+        check(lib.sc4dvar_batch_create(arr, len(self.problems), C.byref(h)))
+        self.h = h
+        self._keep = []
+
+    def hessian_apply(self, Xs, Ys, misfit_only=False, prec=FP64, stream=None):
+        """Ys[b] = (I + H_b) Xs[b] for tensors of shape (k_b, n_b)."""
+        B = len(self.problems)
+        X = (C.c_void_p * B)(*[x.data_ptr() for x in Xs])
+        Y = (C.c_void_p * B)(*[y.data_ptr() for y in Ys])
+        k = (C.c_int * B)(*[x.shape[0] for x in Xs])
+        check(lib.sc4dvar_batch_hessian_apply(self.h, X, Y, k, int(misfit_only), prec, _stream(stream)))
+        return Ys
+
+    def pcg_start(self, rhs, preconds=None, tol=1e-6, prec=FP64, stream=None):
+        B = len(self.problems)
+        R = (C.c_void_p * B)(*[r.data_ptr() for r in rhs])
+        Pc = None
+        if preconds is not None:
+            Pc = (C.c_void_p * B)(*[None if p is None else p.h for p in preconds])
+        self._keep = [rhs, preconds]
+        check(lib.sc4dvar_batch_pcg_start(self.h, Pc, R, tol, prec, _stream(stream)))
+
+    def pcg_step(self, nsteps=1, stream=None):
+        check(lib.sc4dvar_batch_pcg_step(self.h, nsteps, _stream(stream)))
+
+    def pcg_status(self, stream=None):
+        B = len(self.problems)
+        rel, its, st = (C.c_double * B)(), (C.c_int * B)(), (C.c_int * B)()
+        check(lib.sc4dvar_batch_pcg_status(self.h, rel, its, st, _stream(stream)))
+        return list(rel), list(its), list(st)
+
+    def pcg_solution(self, xs, stream=None):
+        B = len(self.problems)
+        X = (C.c_void_p * B)(*[x.data_ptr() for x in xs])
+        check(lib.sc4dvar_batch_pcg_solution(self.h, X, _stream(stream)))
+        return xs
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.sc4dvar_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(problem, k):
+    """Pick the packed FP32 sweep's pairs per thread for this problem by timing."""
+    c = C.c_int()
+    check(lib.sc4dvar_autotune(problem.h, k, C.byref(c)))
+    return c.value
+
+
 def gaussian(seed, stream_id, rows, cols, col0=0, stream=None):
     """(cols, rows) float64 tensor: columns col0.. of the method's Philox stream."""
     torch = _torch()

@@ -118,6 +118,14 @@ SIGNATURES = {
     "sc4dvar_counters": (I, [P, C.POINTER(Counters)]),
     "sc4dvar_counters_reset": (I, [P]),
     "sc4dvar_gaussian": (I, [U64, U64, I, I, C.c_int64, P, P]),
+    "sc4dvar_batch_create": (I, [C.POINTER(P), I, C.POINTER(P)]),
+    "sc4dvar_batch_destroy": (I, [P]),
+    "sc4dvar_batch_hessian_apply": (I, [P, C.POINTER(P), C.POINTER(P), C.POINTER(I), I, I, P]),
+    "sc4dvar_batch_pcg_start": (I, [P, C.POINTER(P), C.POINTER(P), D, I, P]),
+    "sc4dvar_batch_pcg_step": (I, [P, I, P]),
+    "sc4dvar_batch_pcg_status": (I, [P, C.POINTER(D), C.POINTER(I), C.POINTER(I), P]),
+    "sc4dvar_batch_pcg_solution": (I, [P, C.POINTER(P), P]),
+    "sc4dvar_autotune": (I, [P, I, C.POINTER(I)]),
 }
 
 _lib = None

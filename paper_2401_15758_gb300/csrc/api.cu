@@ -223,6 +223,26 @@ static int hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t s
   return SC4DVAR_OK;
 }
 
+// Entry points of the batch module (batch.cu): the same operators, by problem.
+int batch_hvp_one(Prob* P, const void* X, int k, void* Y, int misfit_only, int prec, cudaStream_t st) {
+  if (prec == SC4DVAR_FP64)
+    return hvp_block<double>(P, (const double*)X, P->n, k, (double*)Y, P->n, misfit_only, st);
+  return hvp_block<float>(P, (const float*)X, P->n, k, (float*)Y, P->n, misfit_only, st);
+}
+
+int batch_hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t st) {
+  return hvp_vec(P, p, q, prec, st);
+}
+
+int batch_precond(Prec* pc, const double* r, double* z, int n, cudaStream_t st) {
+  if (pc && pc->l > 0) {
+    SC4_TRY(pc->T.ensure((size_t)pc->l * sizeof(double)));
+    return woodbury_apply(n, pc->l, 1, pc->V, n, pc->dsc, r, n, z, n, pc->T.as<double>(), st);
+  }
+  SC4_CUDA(cudaMemcpyAsync(z, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return SC4DVAR_OK;
+}
+
 static int host_scalar(Prob* P, double* out, cudaStream_t st) {
   return d2h(out, P->scal.as<double>(), 1, st);
 }

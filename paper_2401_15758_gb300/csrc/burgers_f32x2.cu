@@ -447,12 +447,12 @@ __global__ void __launch_bounds__(Bounds2<P>::kThreads, 1) adj_f32x2_kernel(
 // ---------------------------------------------------------------- host
 const size_t kMaxSmem2 = 227 * 1024;
 
-int pairs_per_thread(int Hs) {
+int pairs_per_thread(int Hs, int tuned) {
   static int forced = [] {
     const char* e = getenv("SC4DVAR_PAIRS_P");
     return e ? atoi(e) : 0;
   }();
-  int P = forced > 0 ? forced : std::max(1, std::min(8, Hs / 512));
+  int P = tuned > 0 ? tuned : (forced > 0 ? forced : std::max(1, std::min(8, Hs / 512)));
   if (P != 1 && P != 2 && P != 4 && P != 8) P = 8;
   while (P > 1 && Hs / P < 32) P /= 2;
   while (Hs / P > Bounds2<8>::kThreads * (P >= 8 ? 1 : 2) && P < 8) P *= 2;
@@ -527,7 +527,7 @@ int burgers_tlm_f32x2(const ModelGeom& m, const float* traj_folded, const float*
   const int H = m.n / 2;
   int cl = cluster_for(H, k, 3);
   Geo g = make_geo(m, cl);
-  int P = pairs_per_thread(g.Hs), NT = g.Hs / P;
+  int P = pairs_per_thread(g.Hs, m.pairs_tuned), NT = g.Hs / P;
   size_t smem = (size_t)(2 * g.Hs + g.Hs + 2 * kPad2 + 8 * 32) * sizeof(f2);
   if (cl > 1) {
     SC4_DISPATCH_PAIRS(P, SC4_TRY(launch2(tlm_f32x2_kernel<PP, true>, k * cl, NT, smem, cl, st, g,
@@ -545,7 +545,7 @@ int burgers_adj_f32x2(const ModelGeom& m, const float* traj_folded, const float*
   const int H = m.n / 2;
   int cl = cluster_for(H, k, 4);
   Geo g = make_geo(m, cl);
-  int P = pairs_per_thread(g.Hs), NT = g.Hs / P;
+  int P = pairs_per_thread(g.Hs, m.pairs_tuned), NT = g.Hs / P;
   size_t smem = (size_t)(4 * (g.Hs + 2 * kPad2) + 4 * 32) * sizeof(f2);
   if (cl > 1) {
     SC4_DISPATCH_PAIRS(P, SC4_TRY(launch2(adj_f32x2_kernel<PP, true>, k * cl, NT, smem, cl, st, g,

@@ -14,6 +14,7 @@ struct ModelGeom {
   const int* obs_of_step;   // device [N+1]: observation index at step t, or -1
   const int* obs_idx;       // device [n_t * n_o]
   int fold32 = 0;           // FP32 trajectory copy stored folded (pairs x_i, x_{i+n/2})
+  int pairs_tuned = 0;      // packed FP32 sweeps: pairs per thread chosen by sc4dvar_autotune (0: default)
 };
 
 // FP32 sweeps on grids of at least this many points use packed FP32x2 kernels

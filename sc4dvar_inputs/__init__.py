@@ -293,3 +293,23 @@ def bve_draws(wl: BVEWorkload) -> dict:
         "prior_ell": wl.ell_cells * wl.d,
         "sigma_obs": wl.sigma_frac * float(np.max(np.abs(q0))),
     }
+
+
+def burgers_batch(count: int = 64, seed: int = DEFAULT_SEED):
+    """Uneven batch of Burgers windows: n from {512, ..., 8192}, N_out from
+    {100, 200, 400} and k from {16, 32, 64}, drawn per problem from seed + p;
+    dt_out = 5e-5, nu = 0.005, observations every 10 output steps at every 8th
+    point (each problem its own pattern: a random offset of the 8-point comb)."""
+    out = []
+    for p in range(count):
+        rng = _rng(seed + p, 50)
+        n = int(rng.choice([512, 1024, 2048, 4096, 8192]))
+        n_out = int(rng.choice([100, 200, 400]))
+        k = int(rng.choice([16, 32, 64]))
+        wl = BurgersWorkload(name=f"batch{p}", n=n, nu=0.005, dt_out=5e-5, n_out=n_out, obs_every=10,
+                             obs_stride=8, sigma_obs=0.05, k=k, seed=seed + p)
+        offset = int(rng.integers(0, 8))
+        draws = burgers_draws(wl)
+        draws["obs_idx"] = ((draws["obs_idx"] + offset) % n).astype(np.int32)
+        out.append((wl, draws))
+    return out
