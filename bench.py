@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-gn-step", action="store_true", help="skip the time-to-solution part")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256", "burgers_batch64"],
                     help="the Burgers block (default) or the barotropic vorticity block")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
@@ -259,6 +259,65 @@ def bve_arm(args):
                         "frac": nbytes / t / 1e9 / peak, "traffic": None,
                         "algorithmic_bytes": nbytes},
            "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
+def batch_arm(args):
+    """64 uneven Burgers problems: one graph-replayed batched block Hessian
+    product (FP32 sweeps) per step; HVP/s = sum of the block widths / time."""
+    import torch
+    import paper_2401_15758_gb300 as g
+    import sc4dvar_inputs as si
+    dev = torch.device("cuda", 0)
+    probs, Xs = [], []
+    items = si.burgers_batch(64)
+    for wl, d in items:
+        p = g.Problem.from_workload(wl, d["obs_idx"])
+        xt = torch.tensor(d["x_true0"], device=dev)
+        obs, _ = p.forecast(xt)
+        p.set_observations(obs + wl.sigma_obs * torch.tensor(d["xi_o"].reshape(-1), device=dev))
+        p.set_background(xt + p.prior_sqrt_apply(torch.tensor(d["xi_b"], device=dev)))
+        p.fwd(torch.zeros(wl.n, dtype=torch.float64, device=dev))
+        g.autotune(p, wl.k)
+        probs.append(p)
+        Xs.append(torch.tensor(si.gaussian_matrix(wl.seed, wl.k, wl.n, stream=25), device=dev,
+                               dtype=torch.float32))
+    Ys = [torch.empty_like(x) for x in Xs]
+    b = g.Batch(probs)
+    total_k = sum(x.shape[0] for x in Xs)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, args.warmup)):
+        b.hessian_apply(Xs, Ys, prec=g.FP32)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = g.lib.sc4dvar_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.hessian_apply(Xs, Ys, prec=g.FP32)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(e))
+    launches = g.lib.sc4dvar_launch_count() - l0
+    clk = clocks.stop()
+    t = statistics.mean(ms) / 1e3
+    flops = sum((FLOPS_TLM + FLOPS_ADJ) * wl.n * wl.n_steps * wl.k for wl, _ in items)
+    out = {"metric": METRIC, "value": total_k / t, "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "burgers_batch64: 64 Burgers problems, n in {512..8192}, "
+                                  "N_out in {100,200,400}, k in {16,32,64} per problem",
+                      "problems": 64, "total_k": total_k,
+                      "l2": "256 MiB write before every timed step"},
+           "roofline": {"bound": "alu", "kernel": "batched sweeps (all problems, one graph)",
+                        "achieved": flops / t / 1e12, "peak": FP32_PEAK_ALU / 1e12, "unit": "TFLOP/s",
+                        "frac": flops / t / FP32_PEAK_ALU, "traffic": None},
+           "gpu_launches": int(launches), "graph_launches_per_step": 1, "clocks": clk}
     print(json.dumps(out), flush=True)
 
 
@@ -490,6 +549,8 @@ def main():
         reference_arm(args)
     elif args.workload == "bve_n256":
         bve_arm(args)
+    elif args.workload == "burgers_batch64":
+        batch_arm(args)
     else:
         gpu_arm(args)
 
