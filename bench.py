@@ -180,6 +180,23 @@ def config_dict(wl):
 
 
 # ------------------------------------------------------------------ GPU arm
+def max_over_ranks(dist, value, device):
+    """The largest per-rank value over all ranks (the slowest replica sets the
+    job time); `dist` is torch.distributed or None for one process."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput: every replica processes units_per_rank units (weak
+    scaling, no data-path exchange), the job takes the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def setup_problem(torch, dev):
     import paper_2401_15758_gb300 as g
     import sc4dvar_inputs as si
@@ -373,13 +390,8 @@ def gpu_arm(args):
     if dist:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    hvps = k * args.steps * world
-    value = hvps / (total_ms / 1e3)
+    total_ms = max_over_ranks(dist, sum(ms), dev)
+    value = job_throughput(k * args.steps, world, total_ms / 1e3)
 
     # dominant kernels: ADJ and TLM sweeps timed alone (each call = sweep + one prior FFT pass)
     W = torch.empty((k, wl.m), dtype=torch.float32, device=dev)
