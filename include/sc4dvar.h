@@ -101,6 +101,15 @@ typedef struct {
     const double* prior_symbol; /* SYMBOL: [n] real even Fourier symbol of Gamma^{1/2} */
     double forcing_amp;    /* BVE forcing amplitude (F = amp sin(k y))                */
     int forcing_k;         /* BVE forcing wavenumber                                 */
+    int n_checkpoints;     /* BVE: 0 = keep every RK stage state of the FWD (the sweeps
+                              read them); c in [1, n_steps] = keep only the FP64 state
+                              at c evenly spaced steps (every L = ceil(n_steps / c)
+                              steps) and recompute one segment of L steps at a time
+                              inside each TLM / ADJ sweep and the gradient: device
+                              memory for states falls from 4 N n (12 B + 12 B) to
+                              c n 8 B + 4 L n 12 B at the cost of one extra FWD per
+                              sweep (sqrt-N checkpointing, c ~ sqrt(N)). Results are
+                              identical to c = 0. Burgers: must be 0.              */
     /* BVE (Sec. 5.2, doubly periodic form): q_t = -J_A(psi, q) + nu Lap_h q + F,
        psi = Lap^{-1} q (spectral), J_A Arakawa's Jacobian, Lap_h five-point. */
 } sc4dvar_problem_desc;

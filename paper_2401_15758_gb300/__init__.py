@@ -103,7 +103,7 @@ class Problem:
 
     def __init__(self, *, n, nu, dt, n_steps, obs_steps, obs_idx, sigma_obs,
                  prior_sigma=None, prior_length=None, prior_symbol=None, model=MODEL_BURGERS1D,
-                 grid=None, forcing_amp=0.0, forcing_k=0):
+                 grid=None, forcing_amp=0.0, forcing_k=0, n_checkpoints=0):
         obs_steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
         obs_idx = np.ascontiguousarray(obs_idx, dtype=np.int32)
         d = _abi.ProblemDesc()
@@ -111,6 +111,7 @@ class Problem:
         if model == _abi.MODEL_BVE2D:
             d.nx = d.ny = int(grid)
             d.forcing_amp, d.forcing_k = float(forcing_amp), int(forcing_k)
+            d.n_checkpoints = int(n_checkpoints)
         else:
             d.nx, d.ny = int(n), 1
         d.nu, d.dt, d.n_steps = float(nu), float(dt), int(n_steps)
@@ -143,10 +144,13 @@ class Problem:
                    prior_length=wl.length_b, **kw)
 
     @classmethod
-    def from_bve_workload(cls, wl, draws):
+    def from_bve_workload(cls, wl, draws, n_checkpoints=None):
         """Barotropic vorticity problem: N x N doubly periodic grid (fields of N*N,
-        row-major, y slow), inverse-Helmholtz prior c (I - ell^2 Lap)^{-1}."""
-        return cls(n=wl.n, nu=wl.nu, dt=wl.dt, n_steps=wl.n_steps, obs_steps=wl.obs_steps,
+        row-major, y slow), inverse-Helmholtz prior c (I - ell^2 Lap)^{-1}.
+        n_checkpoints: None takes the workload's (0 = store every stage state)."""
+        if n_checkpoints is None:
+            n_checkpoints = getattr(wl, "n_checkpoints", 0)
+        return cls(n_checkpoints=n_checkpoints, n=wl.n, nu=wl.nu, dt=wl.dt, n_steps=wl.n_steps, obs_steps=wl.obs_steps,
                    obs_idx=draws["obs_idx"], sigma_obs=draws["sigma_obs"],
                    prior_sigma=draws["prior_c"], prior_length=draws["prior_ell"],
                    model=_abi.MODEL_BVE2D, grid=wl.N, forcing_amp=wl.forcing_amp,
@@ -197,6 +201,7 @@ class Problem:
         J = C.c_double()
         d = _torch().empty(self.m, dtype=_torch().float64, device=v.device) if want_d else None
         check(lib.sc4dvar_fwd(self.h, _ptr(v), C.byref(J), _ptr(d), _stream(stream)))
+        self._fwd_gen = getattr(self, "_fwd_gen", 0) + 1
         return (J.value, d) if want_d else J.value
 
     def gradient(self, stream=None, out=None):
@@ -334,6 +339,48 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+_COST_FN = None
+
+
+def _cost_fn():
+    global _COST_FN
+    if _COST_FN is None:
+        torch = _torch()
+
+        class FourDVarCost(torch.autograd.Function):
+            """J(v) = 1/2 |v|^2 + 1/2 sum_i |R_i^{-1/2}(O_i x_i - y_i)|^2, x0 = xb + Gamma^{1/2} v
+            (Eq. 4dvar_cf in the control variable). forward: the FP64 FWD sweep,
+            which leaves the trajectory (or, with checkpointing, the FP64
+            checkpoints) and the residuals in the handle. backward: the discrete
+            adjoint sweep (Eq. 4dvar_gradient), recomputing each checkpoint
+            segment, g_v = v + A^T d, scaled by the incoming gradient."""
+
+            @staticmethod
+            def forward(ctx, v, problem):
+                J = problem.fwd(v.detach().contiguous())
+                ctx.problem = problem
+                ctx.gen = problem._fwd_gen
+                return v.new_tensor(J)
+
+            @staticmethod
+            def backward(ctx, gJ):
+                pr = ctx.problem
+                if getattr(pr, "_fwd_gen", None) != ctx.gen:
+                    raise RuntimeError("the problem ran another FWD after this cost was evaluated; "
+                                       "evaluate the cost again before calling backward")
+                g = pr.gradient()
+                return gJ.to(g.dtype) * g, None
+
+        _COST_FN = FourDVarCost
+    return _COST_FN
+
+
+def cost(problem, v):
+    """Differentiable 4D-Var cost J(v) (a 0-dim FP64 tensor on v's device):
+    J.backward() runs the adjoint sweep of `problem` at the v of this call."""
+    return _cost_fn().apply(v, problem)
 
 
 def autotune(problem, k):

@@ -42,7 +42,7 @@ class ProblemDesc(C.Structure):
         ("n_obs", C.c_int), ("obs_idx", C.POINTER(C.c_int)), ("sigma_obs", C.c_double),
         ("prior_kind", C.c_int), ("prior_sigma", C.c_double), ("prior_length", C.c_double),
         ("prior_symbol", C.POINTER(C.c_double)),
-        ("forcing_amp", C.c_double), ("forcing_k", C.c_int),
+        ("forcing_amp", C.c_double), ("forcing_k", C.c_int), ("n_checkpoints", C.c_int),
     ]
 
 

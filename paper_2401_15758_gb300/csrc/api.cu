@@ -808,8 +808,7 @@ static int fwd_run(Prob* P, const double* v, double* J_host, double* d_out, cuda
   SC4_TRY(prior_any<double, double, double>(P, 1, P->v, n, P->x0, n, P->xb, n, st));
   if (is_bve(P)) {
     SC4_TRY(P->wBve.ensure(std::max(bve_fwd_ws_bytes(P->bve), bve_sweep_ws_bytes(P->bve, 1, 8))));
-    SC4_TRY(bve_fwd(P->bve, P->x0, P->bve_q64, P->bve_p64, P->bve_q32, P->bve_p32, P->y, P->d, nullptr,
-                    nullptr, P->wBve.p, st));
+    SC4_TRY(bve_fwd(P->bve, P->x0, true, P->y, P->d, nullptr, nullptr, P->wBve.p, st));
   } else {
     SC4_TRY(burgers_fwd<double>(P->geom, P->x0, P->traj64, P->traj32, P->y, P->d, nullptr, nullptr, st));
   }
@@ -909,9 +908,12 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
             "BVE grid must be N x N with N a power of two in [16, 1024]");
     SC4_ARG(d->prior_kind == SC4DVAR_PRIOR_INV_HELMHOLTZ && d->prior_sigma > 0 && d->prior_length >= 0,
             "BVE prior: SC4DVAR_PRIOR_INV_HELMHOLTZ with prior_sigma > 0, prior_length >= 0");
+    SC4_ARG(d->n_checkpoints >= 0 && d->n_checkpoints <= d->n_steps,
+            "n_checkpoints must lie in [0, n_steps]");
   } else {
     SC4_ARG(d->nx >= 8 && d->nx <= 8192 && (d->nx & (d->nx - 1)) == 0,
             "Burgers n must be a power of two in [8, 8192]");
+    SC4_ARG(d->n_checkpoints == 0, "checkpointing covers the BVE model (n_checkpoints must be 0)");
   }
   int n = bve ? d->nx * d->ny : d->nx;
   SC4_ARG(d->n_steps >= 1 && d->dt > 0 && d->nu >= 0, "time window");
@@ -948,7 +950,22 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   size_t traj_pts = bve ? 0 : (size_t)(P->N + 1) * n;
   if (bve) {
     const int Ng = d->nx;
-    size_t stages = (size_t)4 * P->N * n;
+    // Checkpointing: L = ceil(N / c) steps per segment; the stage-state buffers
+    // hold one segment, the FP64 checkpoints one state per segment.
+    const int L = d->n_checkpoints > 0 ? (P->N + d->n_checkpoints - 1) / d->n_checkpoints : 0;
+    const int n_seg = L > 0 ? (P->N + L - 1) / L : 0;
+    P->bve.ckpt_every = L;
+    size_t stages = (size_t)4 * (L > 0 ? L : P->N) * n;
+    if (L > 0) {
+      BveGeom tmp{};
+      tmp.N = Ng;
+      if (cudaMalloc(&P->bve_ckpt, (size_t)n_seg * n * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&P->bve_rws, bve_fwd_ws_bytes(tmp)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("problem_create: device allocation of the BVE checkpoints failed");
+        return fail(SC4DVAR_ERR_OOM);
+      }
+    }
     if (cudaMalloc(&P->bve_tw64, (Ng / 2) * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&P->bve_tw32, (Ng / 2) * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&P->bve_poisson, (size_t)n * sizeof(double)) != cudaSuccess ||
@@ -1026,6 +1043,8 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
     b.p64 = P->bve_p64;
     b.q32 = P->bve_q32;
     b.p32 = P->bve_p32;
+    b.ckpt = P->bve_ckpt;
+    b.rws = P->bve_rws;
     if ((rc = bve_setup(b, 0))) return fail(rc);
   } else if ((rc = fft_make_twiddles(n, P->tw, 0))) {
     return fail(rc);
@@ -1057,6 +1076,7 @@ int sc4dvar_problem_destroy(sc4dvar_problem_t P) {
   cudaFree(P->bve_tw64); cudaFree(P->bve_tw32); cudaFree(P->bve_poisson); cudaFree(P->bve_prior);
   cudaFree(P->bve_tabc64); cudaFree(P->bve_tabc32);
   cudaFree(P->bve_q64); cudaFree(P->bve_p64); cudaFree(P->bve_q32); cudaFree(P->bve_p32);
+  cudaFree(P->bve_ckpt); cudaFree(P->bve_rws);
   P->wBve.release(); P->wCplx.release();
   P->wU.release(); P->wW.release(); P->wL.release(); P->part.release(); P->scal.release();
   P->vec.release();
@@ -1105,8 +1125,7 @@ int sc4dvar_forecast(sc4dvar_problem_t P, const double* x0, double* obs, double*
   SC4_ARG(P && x0 && obs, "null argument");
   if (is_bve(P)) {
     SC4_TRY(P->wBve.ensure(std::max(bve_fwd_ws_bytes(P->bve), P->wBve.bytes)));
-    return bve_fwd(P->bve, x0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, obs, xN, P->wBve.p,
-                   S(stream));
+    return bve_fwd(P->bve, x0, false, nullptr, nullptr, obs, xN, P->wBve.p, S(stream));
   }
   return burgers_fwd<double>(P->geom, x0, nullptr, nullptr, nullptr, nullptr, obs, xN, S(stream));
 }

@@ -734,34 +734,42 @@ static int d2f(size_t total, const double* x, float* y, cudaStream_t st) {
   return SC4DVAR_OK;
 }
 
-// FWD in FP64 from x0. When q64/p64 are given, stores the stage states q_s(t),
-// psi_s(t) at row 4 t + s (and FP32 copies when q32/p32 are given); writes the
-// observation outputs. ws: bve_fwd_ws_bytes.
-int bve_fwd(const BveGeom& g, const double* x0, double* q64, double* p64, float* q32, float* p32,
-            const double* y, double* d_out, double* obs_out, double* xN, void* ws, cudaStream_t st) {
+// Observation outputs of the FP64 state x at step t (when t is an observation step).
+static int fwd_obs(const BveGeom& g, int t, const double* x, const double* y, double* d_out,
+                   double* obs_out, cudaStream_t st) {
+  int oi = g.obs_of_step_h[t];
+  if (oi < 0 || !(d_out || obs_out)) return SC4DVAR_OK;
+  bve_fwd_obs_kernel<<<div_up(g.n_o, 256), 256, 0, st>>>(g.n_o, g.obs_idx + (size_t)oi * g.n_o, x,
+                                                         oi * g.n_o, y, d_out, obs_out, 1.0 / g.sigma);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+// FP64 RK4 steps [t0, t1) from the state x (advanced in place; ws_fwd laid out
+// as x, acc, two stage buffers, psi scratch, complex FFT buffer). Stage states
+// go to row 4 (t - t0) + s of q64 / p64 / q32 / p32 (each may be null);
+// observation outputs at the steps in [t0, t1); with save_ckpt, the state at
+// every multiple of g.ckpt_every goes to its checkpoint slot.
+static int fwd_steps(const BveGeom& g, void* ws_fwd, int t0, int t1, double* q64, double* p64,
+                     float* q32, float* p32, const double* y, double* d_out, double* obs_out,
+                     bool save_ckpt, cudaStream_t st) {
   const int N = g.N;
   const size_t n = (size_t)N * N;
-  double* x = reinterpret_cast<double*>(ws);
+  double* x = reinterpret_cast<double*>(ws_fwd);
   double* acc = x + n;
   double* S[2] = {acc + n, acc + 2 * n};
   double* ptmp = acc + 3 * n;
   void* cbuf = ptmp + n;
   StencilConsts sc = consts(g);
-  SC4_TRY(copy_fields<double>(n, x0, x, st));
   const dim3 grid = sgrid(N, 1), blk(32, 8);
-  for (int t = 0;; ++t) {
-    int oi = g.obs_of_step_h[t];
-    if (oi >= 0 && (d_out || obs_out)) {
-      bve_fwd_obs_kernel<<<div_up(g.n_o, 256), 256, 0, st>>>(g.n_o, g.obs_idx + (size_t)oi * g.n_o, x,
-                                                             oi * g.n_o, y, d_out, obs_out,
-                                                             1.0 / g.sigma);
-      SC4_LAUNCH_CHECK();
-    }
-    if (t == g.Nsteps) break;
+  for (int t = t0; t < t1; ++t) {
+    SC4_TRY(fwd_obs(g, t, x, y, d_out, obs_out, st));
+    if (save_ckpt && g.ckpt_every > 0 && t % g.ckpt_every == 0)
+      SC4_TRY(copy_fields<double>(n, x, g.ckpt + (size_t)(t / g.ckpt_every) * n, st));
     for (int s = 0; s < 4; ++s) {
       const double* Xs = (s == 0) ? x : S[(s - 1) & 1];
       double* nxt = (s < 3) ? S[s & 1] : nullptr;
-      size_t row = (size_t)(4 * t + s) * n;
+      size_t row = (size_t)(4 * (t - t0) + s) * n;
       double* ps = p64 ? p64 + row : ptmp;
       SC4_TRY(fft2_apply<double, double, double, double>(g, 1, Xs, (int)n, ps, (int)n,
                                                          (const double*)nullptr, 0, g.poisson, cbuf, st));
@@ -774,8 +782,50 @@ int bve_fwd(const BveGeom& g, const double* x0, double* q64, double* p64, float*
       SC4_LAUNCH_CHECK();
     }
   }
+  return SC4DVAR_OK;
+}
+
+// FWD in FP64 from x0 with the observation outputs (d = R^{-1/2}(O x - y) and/or
+// O x). With `store`, keeps what the sweeps need: every stage state (FP64 and
+// FP32 copies), or with checkpointing only the FP64 checkpoints. ws: bve_fwd_ws_bytes.
+int bve_fwd(const BveGeom& g, const double* x0, bool store, const double* y, double* d_out,
+            double* obs_out, double* xN, void* ws, cudaStream_t st) {
+  const size_t n = (size_t)g.N * g.N;
+  double* x = reinterpret_cast<double*>(ws);
+  SC4_TRY(copy_fields<double>(n, x0, x, st));
+  const bool full = store && g.ckpt_every == 0;
+  SC4_TRY(fwd_steps(g, ws, 0, g.Nsteps, full ? g.q64 : nullptr, full ? g.p64 : nullptr,
+                    full ? g.q32 : nullptr, full ? g.p32 : nullptr, y, d_out, obs_out,
+                    store && g.ckpt_every > 0, st));
+  SC4_TRY(fwd_obs(g, g.Nsteps, x, y, d_out, obs_out, st));
   if (xN) SC4_TRY(copy_fields<double>(n, x, xN, st));
   return SC4DVAR_OK;
+}
+
+// Steps [t0, t1) of checkpoint segment j and the row base of its stage states.
+struct Segment {
+  int t0, t1;
+};
+static Segment segment_of(const BveGeom& g, int j) {
+  const int L = g.ckpt_every > 0 ? g.ckpt_every : g.Nsteps;
+  return {j * L, std::min((j + 1) * L, g.Nsteps)};
+}
+static int n_segments(const BveGeom& g) {
+  return g.ckpt_every > 0 ? (g.Nsteps + g.ckpt_every - 1) / g.ckpt_every : 1;
+}
+
+// With checkpointing: recompute the stage states of segment j from its
+// checkpoint into the segment buffers (the precision the sweep of type T reads).
+// The same kernels in the same order as the FWD give bit-identical states.
+template <typename T>
+static int recompute_segment(const BveGeom& g, int j, cudaStream_t st) {
+  if (g.ckpt_every == 0) return SC4DVAR_OK;
+  const size_t n = (size_t)g.N * g.N;
+  const Segment sg = segment_of(g, j);
+  SC4_TRY(copy_fields<double>(n, g.ckpt + (size_t)j * n, reinterpret_cast<double*>(g.rws), st));
+  const bool f64 = sizeof(T) == 8;
+  return fwd_steps(g, g.rws, sg.t0, sg.t1, f64 ? g.q64 : nullptr, f64 ? g.p64 : nullptr,
+                   f64 ? nullptr : g.q32, f64 ? nullptr : g.p32, nullptr, nullptr, nullptr, false, st);
 }
 
 template <typename T>
@@ -805,26 +855,34 @@ int bve_tlm(const BveGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* 
     SC4_CUDA(cudaMemcpyAsync(dx + (size_t)c * n, U0 + (size_t)c * ldu, n * sizeof(T),
                              cudaMemcpyDeviceToDevice, st));
   const dim3 grid = sgrid(N, k), blk(32, 8);
-  for (int t = 0;; ++t) {
+  auto gather = [&](int t) -> int {
     int oi = g.obs_of_step_h[t];
     if (oi >= 0) {
       bve_gather_kernel<T><<<dim3(div_up(g.n_o, 256), k), 256, 0, st>>>(
           g.n_o, g.obs_idx + (size_t)oi * g.n_o, dx, n, W, ldw, oi * g.n_o, inv_sigma);
       SC4_LAUNCH_CHECK();
     }
-    if (t == g.Nsteps) break;
-    for (int s = 0; s < 4; ++s) {
-      const T* cur = (s == 0) ? dx : S[(s - 1) & 1];
-      T* nxt = (s < 3) ? S[s & 1] : nullptr;
-      size_t row = (size_t)(4 * t + s) * n;
-      SC4_TRY(fft2_apply<T, T, T, T>(g, k, cur, (int)n, dpsi, (int)n, (const T*)nullptr, 0, g.poisson,
-                                     cbuf, st));
-      bve_tlm_stage_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, (T)g.h, qbase<T>(g) + row,
-                                                    pbase<T>(g) + row, cur, dpsi, acc, dx, nxt, n);
-      SC4_LAUNCH_CHECK();
+    return SC4DVAR_OK;
+  };
+  for (int j = 0; j < n_segments(g); ++j) {
+    const Segment sg = segment_of(g, j);
+    SC4_TRY(recompute_segment<T>(g, j, st));
+    const int base = g.ckpt_every > 0 ? sg.t0 : 0;
+    for (int t = sg.t0; t < sg.t1; ++t) {
+      SC4_TRY(gather(t));
+      for (int s = 0; s < 4; ++s) {
+        const T* cur = (s == 0) ? dx : S[(s - 1) & 1];
+        T* nxt = (s < 3) ? S[s & 1] : nullptr;
+        size_t row = (size_t)(4 * (t - base) + s) * n;
+        SC4_TRY(fft2_apply<T, T, T, T>(g, k, cur, (int)n, dpsi, (int)n, (const T*)nullptr, 0, g.poisson,
+                                       cbuf, st));
+        bve_tlm_stage_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, (T)g.h, qbase<T>(g) + row,
+                                                      pbase<T>(g) + row, cur, dpsi, acc, dx, nxt, n);
+        SC4_LAUNCH_CHECK();
+      }
     }
   }
-  return SC4DVAR_OK;
+  return gather(g.Nsteps);
 }
 
 // ADJ of k directions: Out = lam_0 forced by W. ws as for bve_tlm.
@@ -843,25 +901,30 @@ int bve_adj(const BveGeom& g, const T* W, int ldw, int k, T* Out, int ldo, void*
   SC4_CUDA(cudaMemsetAsync(lam, 0, nk * sizeof(T), st));
   const dim3 grid = sgrid(N, k), blk(32, 8);
   const T h = (T)g.h;
-  for (int t = g.Nsteps; t >= 1; --t) {
-    int oi = g.obs_of_step_h[t];
-    if (oi >= 0) {
-      bve_scatter_kernel<T><<<dim3(div_up(g.n_o, 256), k), 256, 0, st>>>(
-          g.n_o, g.obs_idx + (size_t)oi * g.n_o, W, ldw, oi * g.n_o, lam, n, inv_sigma);
-      SC4_LAUNCH_CHECK();
-    }
-    SC4_TRY(scale_fields<T>(nk, h * (T)(1.0 / 6.0), lam, K[0], st));  // kappa_4 = h b_4 lam
-    for (int s = 3; s >= 0; --s) {
-      const T* kap = K[(3 - s) & 1];
-      T* knext = K[(4 - s) & 1];
-      size_t row = (size_t)(4 * (t - 1) + s) * n;
-      bve_adj_jac_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, qbase<T>(g) + row, kap, t12, n);
-      SC4_LAUNCH_CHECK();
-      SC4_TRY(fft2_apply<T, T, T, T>(g, k, t12, (int)n, t12, (int)n, (const T*)nullptr, 0, g.poisson,
-                                     cbuf, st));
-      bve_adj_stage_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, h, pbase<T>(g) + row, kap, t12, th, lam,
-                                                    s > 0 ? knext : nullptr, n);
-      SC4_LAUNCH_CHECK();
+  for (int j = n_segments(g) - 1; j >= 0; --j) {
+    const Segment sg = segment_of(g, j);
+    SC4_TRY(recompute_segment<T>(g, j, st));
+    const int base = g.ckpt_every > 0 ? sg.t0 : 0;
+    for (int t = sg.t1; t > sg.t0; --t) {
+      int oi = g.obs_of_step_h[t];
+      if (oi >= 0) {
+        bve_scatter_kernel<T><<<dim3(div_up(g.n_o, 256), k), 256, 0, st>>>(
+            g.n_o, g.obs_idx + (size_t)oi * g.n_o, W, ldw, oi * g.n_o, lam, n, inv_sigma);
+        SC4_LAUNCH_CHECK();
+      }
+      SC4_TRY(scale_fields<T>(nk, h * (T)(1.0 / 6.0), lam, K[0], st));  // kappa_4 = h b_4 lam
+      for (int s = 3; s >= 0; --s) {
+        const T* kap = K[(3 - s) & 1];
+        T* knext = K[(4 - s) & 1];
+        size_t row = (size_t)(4 * (t - 1 - base) + s) * n;
+        bve_adj_jac_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, qbase<T>(g) + row, kap, t12, n);
+        SC4_LAUNCH_CHECK();
+        SC4_TRY(fft2_apply<T, T, T, T>(g, k, t12, (int)n, t12, (int)n, (const T*)nullptr, 0, g.poisson,
+                                       cbuf, st));
+        bve_adj_stage_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, h, pbase<T>(g) + row, kap,
+                                                      t12, th, lam, s > 0 ? knext : nullptr, n);
+        SC4_LAUNCH_CHECK();
+      }
     }
   }
   for (int c = 0; c < k; ++c)

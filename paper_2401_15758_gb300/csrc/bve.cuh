@@ -22,18 +22,24 @@ struct BveGeom {
   float* poisson_c32;
   double* prior_c64;
   float* prior_c32;
-  const double* q64;         // stored stage states, row 4 t + s
-  const double* p64;
-  const float* q32;
-  const float* p32;
+  // Stored stage states q_s(t), psi_s(t) at row 4 t + s. With checkpointing
+  // (ckpt_every = L > 0) they hold one segment of L steps at row 4 (t - t0) + s,
+  // recomputed from the FP64 checkpoint of the segment by every sweep.
+  double* q64;
+  double* p64;
+  float* q32;
+  float* p32;
+  int ckpt_every;            // L: steps per checkpoint segment, 0 = store every stage state
+  double* ckpt;              // device [ceil(Nsteps / L) * N*N] FP64 states at steps 0, L, 2L, ...
+  void* rws;                 // device recompute workspace (bve_fwd_ws_bytes)
 };
 
 int bve_setup(BveGeom& g, cudaStream_t st);
 template <typename R, typename RI, typename RO, typename RZ>
 int fft2_apply(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, const RZ* Z, int ldz,
                const double* table, void* cbuf, cudaStream_t st);
-int bve_fwd(const BveGeom& g, const double* x0, double* q64, double* p64, float* q32, float* p32,
-            const double* y, double* d_out, double* obs_out, double* xN, void* ws, cudaStream_t st);
+int bve_fwd(const BveGeom& g, const double* x0, bool store, const double* y, double* d_out,
+            double* obs_out, double* xN, void* ws, cudaStream_t st);
 template <typename T>
 int bve_tlm(const BveGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* ws, cudaStream_t st);
 template <typename T>

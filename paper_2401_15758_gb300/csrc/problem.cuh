@@ -61,6 +61,8 @@ struct sc4dvar_problem_s {
   float* bve_tabc32 = nullptr;
   double *bve_q64 = nullptr, *bve_p64 = nullptr;
   float *bve_q32 = nullptr, *bve_p32 = nullptr;
+  double* bve_ckpt = nullptr;  // checkpoint states (checkpointing only)
+  void* bve_rws = nullptr;     // segment recompute workspace (checkpointing only)
   sc4::Buf wBve, wCplx;
   // scratch: block operator work arrays, reductions, small host-visible scalars
   sc4::Buf wU, wW, wL, part, scal, vec;

@@ -213,6 +213,7 @@ class BVEWorkload:
     ell_cells: float = 4.0
     prior_frac: float = 0.1
     sigma_frac: float = 0.02
+    n_checkpoints: int = 0
 
     @property
     def n(self) -> int:
@@ -245,7 +246,8 @@ class BVEWorkload:
 
 BVE_WORKLOADS = {
     "bve_n256": BVEWorkload(name="bve_n256", N=256, nu=1e-4, n_steps=200, obs_every=10, k=256),
-    "bve_n1024": BVEWorkload(name="bve_n1024", N=1024, nu=1e-4, n_steps=256, obs_every=10, k=512),
+    "bve_n1024": BVEWorkload(name="bve_n1024", N=1024, nu=1e-4, n_steps=256, obs_every=10, k=512,
+                             n_checkpoints=16),
 }
 
 
