@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-gn-step", action="store_true", help="skip the time-to-solution part")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256", "burgers_batch64"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256", "bve_n1024", "burgers_batch64"],
                     help="the Burgers block (default) or the barotropic vorticity block")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
@@ -221,7 +221,6 @@ def setup_problem(torch, dev):
 # field passes); per ADJ stage one Jacobian pass (2), the multiplier (6) and
 # the stage kernel (6): 4 x (12 + 14) = 104 field passes per step.
 BVE_PASSES_PER_STEP = 104
-BVE_K = 256
 
 
 def bve_arm(args):
@@ -229,7 +228,7 @@ def bve_arm(args):
     import paper_2401_15758_gb300 as g
     import sc4dvar_inputs as si
     dev = torch.device("cuda", 0)
-    wl = si.bve_workload("bve_n256")
+    wl = si.bve_workload(args.workload)
     d = si.bve_draws(wl)
     prob = g.Problem.from_bve_workload(wl, d)
     xt = torch.tensor(d["x_true0"], device=dev)
@@ -237,7 +236,7 @@ def bve_arm(args):
     prob.set_observations(obs + d["sigma_obs"] * torch.tensor(d["xi_o"].reshape(-1), device=dev))
     prob.set_background(xt + prob.prior_sqrt_apply(torch.tensor(d["xi_b"], device=dev)))
     prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device=dev))
-    k = BVE_K
+    k = wl.k
     X = torch.tensor(si.gaussian_matrix(wl.seed, k, wl.n, stream=23), device=dev, dtype=torch.float32)
     Y = torch.empty_like(X)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -260,6 +259,19 @@ def bve_arm(args):
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     launches = g.lib.sc4dvar_launch_count() - l0
+    # gradient through the autograd cost: forward = FWD (keeps the checkpoints),
+    # backward = adjoint sweep recomputing each segment
+    v = torch.zeros(wl.n, dtype=torch.float64, device=dev, requires_grad=True)
+    grad_ms = []
+    for i in range(4):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v.grad = None
+        a.record(stream)
+        g.cost(prob, v).backward()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            grad_ms.append(a.elapsed_time(b))
     clk = clocks.stop()
     t = statistics.mean(ms) / 1e3
     nbytes = BVE_PASSES_PER_STEP * wl.n * 4 * wl.n_steps * k
@@ -267,10 +279,13 @@ def bve_arm(args):
     out = {"metric": METRIC, "value": k / t, "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"bve_n256: doubly periodic barotropic vorticity {wl.N}x{wl.N}, "
-                                  f"{wl.n_steps} RK4 steps, m={wl.m}, block k={k}, FP32 sweeps",
+           "config": {"workload": f"{wl.name}: doubly periodic barotropic vorticity {wl.N}x{wl.N}, "
+                                  f"{wl.n_steps} RK4 steps, m={wl.m}, block k={k}, FP32 sweeps"
+                                  + (f", {wl.n_checkpoints} FP64 checkpoints" if wl.n_checkpoints else ""),
                       "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": k,
+                      "checkpoints": wl.n_checkpoints,
                       "l2": "256 MiB write before every timed step"},
+           "gradient_ms": statistics.mean(grad_ms),
            "roofline": {"bound": "hbm", "kernel": "block Hessian product (all sweep kernels)",
                         "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": nbytes / t / 1e9 / peak, "traffic": None,
@@ -541,7 +556,7 @@ def profile_case_bve():
     prob = g.Problem.from_bve_workload(wl, d)
     prob.set_background(torch.tensor(d["x_true0"], device="cuda"))
     prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
-    X = torch.tensor(si.gaussian_matrix(wl.seed, BVE_K, wl.n, stream=23), device="cuda",
+    X = torch.tensor(si.gaussian_matrix(wl.seed, wl.k, wl.n, stream=23), device="cuda",
                      dtype=torch.float32)
     W = prob.tlm_block(X, prec=g.FP32)
     prob.adj_block(W, prec=g.FP32)
@@ -559,7 +574,7 @@ def main():
         return
     if args.impl == "reference":
         reference_arm(args)
-    elif args.workload == "bve_n256":
+    elif args.workload in ("bve_n256", "bve_n1024"):
         bve_arm(args)
     elif args.workload == "burgers_batch64":
         batch_arm(args)
