@@ -263,42 +263,103 @@ __global__ void __launch_bounds__(256) wfft_rows_fwd(int N, int k, const RI* __r
   for (int r = 0; r < R; ++r) out[r * 32 + lane] = v[r];
 }
 
-// columns: forward along y (DIF), symbol at bit-reversed (ky, kx), inverse (DIT)
-template <typename C, int R>
-__global__ void __launch_bounds__(256) wfft_cols(int N, int logN, C* cbuf,
-                                                 const typename CplxOf<C>::R* __restrict__ tcol,
-                                                 const C* __restrict__ tw, int CB) {
+// Column pass of the 2D multiplier (forward transform along y, symbol,
+// inverse transform along y) with lanes mapped to columns: a block owns CB
+// adjacent columns of one complex field and all N rows, thread (g, c) =
+// (tid / CB, tid % CB), so every load and store is a full row segment of the
+// block and no butterfly crosses lanes. A thread holds R = N / G values of its
+// column: rows g + G r (interleaved layout) or rows g R + r (blocked layout;
+// G^2 <= N keeps spans below G inside a thread there). Forward DIF: spans
+// N/2 .. G interleaved, one shared-memory transpose, spans G/2 .. 1 blocked;
+// multiply by the symbol at the bit-reversed (ky, kx) that the DIF leaves;
+// inverse DIT: spans 1 .. G/2 blocked, transpose back, G .. N/2 interleaved.
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+
+template <typename C, int N, int CB, int G>
+__global__ void __launch_bounds__(G * CB) wfft_cols2(C* cbuf, const typename CplxOf<C>::R* __restrict__ tab,
+                                                     const C* __restrict__ tw) {
+  constexpr int R = N / G;
+  static_assert(G * G <= N && R >= 2, "two-phase column split needs G^2 <= N");
   using Rl = typename CplxOf<C>::R;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* tile = reinterpret_cast<C*>(smraw);  // [N][CB+1]
-  const int ld = CB + 1, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int p = blockIdx.y, i0 = blockIdx.x * CB;
-  C* g = cbuf + (size_t)p * N * N;
-  for (int it = threadIdx.x; it < N * CB; it += blockDim.x) {
-    int j = it / CB, c = it - j * CB;
-    tile[j * ld + c] = g[(size_t)j * N + i0 + c];
-  }
-  __syncthreads();
-  for (int c = wid; c < CB; c += 8) {
-    C v[R];
+  C* tile = reinterpret_cast<C*>(smraw);  // [N][CB]
+  const int c = threadIdx.x % CB, gi = threadIdx.x / CB;
+  const int col = blockIdx.x * CB + c;
+  C* gcol = cbuf + (size_t)blockIdx.y * N * N + col;
+  C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = tile[(r * 32 + lane) * ld + c];
-    warp_fft_dif<C, R>(v, lane, tw, N, -1);
-    const Rl* tc = tcol + (size_t)(i0 + c) * N;
+  for (int r = 0; r < R; ++r) v[r] = gcol[(size_t)(gi + G * r) * N];
+  // forward DIF, interleaved rows j = gi + G r: span h = hr G
+#pragma unroll
+  for (int hr = R / 2; hr >= 1; hr >>= 1) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      Rl sv = __ldg(tc + r * 32 + lane);
-      v[r] = cmk<C>(v[r].x * sv, v[r].y * sv);
+      if (r & hr) continue;
+      const int jm = gi + G * (r & (hr - 1));  // j mod h
+      C w = twid(tw, jm * (N / (2 * hr * G)), -1);
+      C u = v[r], x = v[r + hr];
+      v[r] = cadd(u, x);
+      v[r + hr] = cmulc(w, csub(u, x));
     }
-    warp_fft_dit<C, R>(v, lane, tw, N, +1);
+  }
 #pragma unroll
-    for (int r = 0; r < R; ++r) tile[(r * 32 + lane) * ld + c] = v[r];
-  }
+  for (int r = 0; r < R; ++r) tile[(gi + G * r) * CB + c] = v[r];
   __syncthreads();
-  for (int it = threadIdx.x; it < N * CB; it += blockDim.x) {
-    int j = it / CB, c = it - j * CB;
-    g[(size_t)j * N + i0 + c] = tile[j * ld + c];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = tile[(gi * R + r) * CB + c];
+  // forward DIF, blocked rows j = gi R + r: span h < G, j mod h = r mod h
+#pragma unroll
+  for (int h = G / 2; h >= 1; h >>= 1) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & h) continue;
+      C w = twid(tw, (r & (h - 1)) * (N / (2 * h)), -1);
+      C u = v[r], x = v[r + h];
+      v[r] = cadd(u, x);
+      v[r + h] = cmulc(w, csub(u, x));
+    }
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const Rl sv = __ldg(tab + (size_t)(gi * R + r) * N + col);
+    v[r] = cmk<C>(v[r].x * sv, v[r].y * sv);
+  }
+  // inverse DIT, blocked rows: spans 1 .. G/2
+#pragma unroll
+  for (int h = 1; h < G; h <<= 1) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & h) continue;
+      C w = twid(tw, (r & (h - 1)) * (N / (2 * h)), +1);
+      C t = cmulc(w, v[r + h]);
+      v[r + h] = csub(v[r], t);
+      v[r] = cadd(v[r], t);
+    }
+  }
+  // each thread rewrites exactly the slots it read, so no barrier is needed here
+#pragma unroll
+  for (int r = 0; r < R; ++r) tile[(gi * R + r) * CB + c] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = tile[(gi + G * r) * CB + c];
+  // inverse DIT, interleaved rows: spans G .. N/2
+#pragma unroll
+  for (int hr = 1; hr < R; hr <<= 1) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & hr) continue;
+      const int jm = gi + G * (r & (hr - 1));
+      C w = twid(tw, jm * (N / (2 * hr * G)), +1);
+      C t = cmulc(w, v[r + hr]);
+      v[r + hr] = csub(v[r], t);
+      v[r] = cadd(v[r], t);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) gcol[(size_t)(gi + G * r) * N] = v[r];
 }
 
 // rows inverse: bit-reversed kx in (DIT), natural x out, scaled 1/N^2 (+ Z)
@@ -342,15 +403,16 @@ __global__ void bve_twiddle_kernel(int N, double2* tw64, float2* tw32) {
   }
 }
 
-// Column-kernel copy of a symbol table: entry (c, i) = S(ky = bitrev(i), kx =
-// bitrev(c)) at c * N + i, in the real type of the transform (the warp FFTs
-// leave both wavenumbers in bit-reversed order), so a lane's lookup is contiguous.
+// Column-pass copy of a symbol table: entry (j, i) = S(ky = bitrev(j), kx =
+// bitrev(i)) at j * N + i, in the real type of the transform (the row and
+// column DIFs leave both wavenumbers in bit-reversed order), so the lanes of a
+// row segment read adjacent entries.
 template <typename R>
-__global__ void bve_table_cols_kernel(int N, int logN, const double* __restrict__ table, R* out) {
+__global__ void bve_table_brev_kernel(int N, int logN, const double* __restrict__ table, R* out) {
   size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (idx < (size_t)N * N) {
-    int c = (int)(idx / N), i = (int)(idx % N);
-    out[idx] = (R)table[(size_t)brev_n(i, logN) * N + brev_n(c, logN)];
+    int j = (int)(idx / N), i = (int)(idx % N);
+    out[idx] = (R)table[(size_t)brev_n(j, logN) * N + brev_n(i, logN)];
   }
 }
 
@@ -598,8 +660,8 @@ __global__ void bve_fwd_obs_kernel(int n_o, const int* __restrict__ sites, const
 // ------------------------------------------------------------------ host
 static int log2i(int n) { return 31 - __builtin_clz((unsigned)n); }
 
-// The column-ordered copy of `table` in the transform's real type.
-static const void* table_cols(const BveGeom& g, const double* table, size_t rb) {
+// The bit-reversed copy of `table` in the transform's real type.
+static const void* table_brev(const BveGeom& g, const double* table, size_t rb) {
   if (table == g.poisson) return rb == 4 ? (const void*)g.poisson_c32 : (const void*)g.poisson_c64;
   return rb == 4 ? (const void*)g.prior_c32 : (const void*)g.prior_c64;
 }
@@ -611,19 +673,27 @@ template <> const float2* tw_of<float2>(const BveGeom& g) { return g.tw32; }
 
 
 
+// Column-pass shape: CB columns per block (a 128-byte row segment for FP32
+// complex, 128 bytes for FP64 complex with CB = 8), G row groups, G^2 <= N.
+template <typename C>
+struct ColShape {
+  static constexpr int CB = sizeof(C) == 8 ? 16 : 8;
+};
+constexpr int col_groups(int N) { return N >= 1024 ? 32 : N >= 256 ? 16 : N >= 64 ? 8 : 4; }
+
 template <typename C, typename RI, typename RO, typename RZ, int RR>
 static int wfft2(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, const RZ* Z, int ldz,
                  const double* table, C* cb, cudaStream_t st) {
-  const int N = g.N, logN = log2i(N), pairs = (k + 1) / 2;
-  const int CB = (sizeof(C) == 8 || N <= 512) ? 16 : 8;
-  size_t smc = (size_t)N * (CB + 1) * sizeof(C);
-  auto kc = wfft_cols<C, RR>;
+  constexpr int N = RR * 32, CB = ColShape<C>::CB, G = col_groups(N);
+  const int pairs = (k + 1) / 2;
+  const size_t smc = (size_t)N * CB * sizeof(C);
+  auto kc = wfft_cols2<C, N, CB, G>;
   SC4_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
   wfft_rows_fwd<C, RI, RR><<<dim3(div_up(N, 8), pairs), 256, 0, st>>>(N, k, X, ldx, cb, tw_of<C>(g));
   SC4_LAUNCH_CHECK();
   using Rl = typename CplxOf<C>::R;
-  const Rl* tcol = reinterpret_cast<const Rl*>(table_cols(g, table, sizeof(Rl)));
-  kc<<<dim3(N / CB, pairs), 256, smc, st>>>(N, logN, cb, tcol, tw_of<C>(g), CB);
+  const Rl* tab = reinterpret_cast<const Rl*>(table_brev(g, table, sizeof(Rl)));
+  kc<<<dim3(N / CB, pairs), G * CB, smc, st>>>(cb, tab, tw_of<C>(g));
   SC4_LAUNCH_CHECK();
   wfft_rows_inv<C, RO, RZ, RR><<<dim3(div_up(N, 8), pairs), 256, 0, st>>>(N, k, cb, Y, ldy, Z, ldz,
                                                                           tw_of<C>(g));
@@ -679,13 +749,13 @@ int bve_setup(BveGeom& g, cudaStream_t st) {
   SC4_LAUNCH_CHECK();
   const int logN = log2i(N);
   const unsigned nb = (unsigned)((nn + 255) / 256);
-  bve_table_cols_kernel<double><<<nb, 256, 0, st>>>(N, logN, g.poisson, g.poisson_c64);
+  bve_table_brev_kernel<double><<<nb, 256, 0, st>>>(N, logN, g.poisson, g.poisson_c64);
   SC4_LAUNCH_CHECK();
-  bve_table_cols_kernel<float><<<nb, 256, 0, st>>>(N, logN, g.poisson, g.poisson_c32);
+  bve_table_brev_kernel<float><<<nb, 256, 0, st>>>(N, logN, g.poisson, g.poisson_c32);
   SC4_LAUNCH_CHECK();
-  bve_table_cols_kernel<double><<<nb, 256, 0, st>>>(N, logN, g.prior, g.prior_c64);
+  bve_table_brev_kernel<double><<<nb, 256, 0, st>>>(N, logN, g.prior, g.prior_c64);
   SC4_LAUNCH_CHECK();
-  bve_table_cols_kernel<float><<<nb, 256, 0, st>>>(N, logN, g.prior, g.prior_c32);
+  bve_table_brev_kernel<float><<<nb, 256, 0, st>>>(N, logN, g.prior, g.prior_c32);
   SC4_LAUNCH_CHECK();
   return SC4DVAR_OK;
 }

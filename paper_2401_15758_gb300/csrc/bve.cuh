@@ -17,7 +17,7 @@ struct BveGeom {
   float2* tw32;
   double* poisson;           // device [N*N] symbol -1/|kappa|^2
   double* prior;             // device [N*N] symbol of Gamma^{1/2}
-  // column-kernel copies of both symbols (bit-reversed, column-major), FP64 / FP32
+  // column-pass copies of both symbols (both wavenumbers bit-reversed), FP64 / FP32
   double* poisson_c64;
   float* poisson_c32;
   double* prior_c64;

@@ -25,7 +25,7 @@ def make_bve(N, n_steps, obs_every):
     return wl, prob, ref
 
 
-CASES = [(32, 20, 5), (64, 12, 4), (256, 4, 2)]
+CASES = [(16, 10, 5), (32, 20, 5), (64, 12, 4), (128, 6, 3), (256, 4, 2), (512, 2, 1)]
 
 
 @pytest.fixture(scope="module", params=CASES, ids=lambda c: f"N{c[0]}")
@@ -98,3 +98,18 @@ def test_bve_gauss_newton_matches_oracle():
     assert abs(rec[1]["J"] - info[1]["J"]) <= 1e-9 * abs(info[1]["J"])
     assert abs(rec[0]["pcg_its"] - info[0]["pcg_its"]) <= 1
     assert rel(v.cpu().numpy(), vr) <= 1e-6
+
+
+@pytest.mark.parametrize("N", [16, 32, 64, 128, 256, 512, 1024])
+def test_prior_multiplier_every_grid(N):
+    """The 2D multiplier of every grid size (each size is its own kernel
+    instantiation) against numpy's FFT, on an odd number of fields."""
+    import paper_2401_15758_gb300 as g
+    from oracle import bve
+    wl = si.bve_workload("bve_n256", N=N, n_steps=2, obs_every=1)
+    draws = si.bve_draws(wl)
+    prob = g.Problem.from_bve_workload(wl, draws)
+    sym = bve.inv_helmholtz_sqrt_symbol(N, draws["prior_c"], draws["prior_ell"])
+    X = np.random.default_rng(N).standard_normal((3, wl.n))
+    Y = prob.prior_sqrt_apply(torch.tensor(X, device="cuda")).cpu().numpy()
+    assert rel(Y, bve.apply_symbol_2d(sym, X.T, N).T) <= 1e-12
