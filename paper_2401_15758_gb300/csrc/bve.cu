@@ -434,47 +434,6 @@ struct St9 {
   T c, e, w, n, s, ne, nw, se, sw;
 };
 
-// Values (x_{i-1}, x_i, x_{i+1}) of row j of a periodic field.
-template <typename T>
-struct Row3 {
-  T w, c, e;
-};
-
-template <typename T>
-__device__ __forceinline__ Row3<T> ld3(const T* __restrict__ f, int N, int i, int j) {
-  const T* r = f + (size_t)(j & (N - 1)) * N;
-  Row3<T> v;
-  v.w = __ldg(r + ((i - 1) & (N - 1)));
-  v.c = __ldg(r + i);
-  v.e = __ldg(r + ((i + 1) & (N - 1)));
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ St9<T> st9(const Row3<T>& s, const Row3<T>& m, const Row3<T>& n) {
-  St9<T> v;
-  v.c = m.c; v.e = m.e; v.w = m.w;
-  v.n = n.c; v.s = s.c; v.ne = n.e; v.nw = n.w; v.se = s.e; v.sw = s.w;
-  return v;
-}
-
-// A sliding three-row window over one field: rows j-1, j, j+1 in registers.
-template <typename T>
-struct Win {
-  Row3<T> s, m, n;
-  __device__ __forceinline__ void init(const T* f, int N, int i, int j) {
-    s = ld3(f, N, i, j - 1);
-    m = ld3(f, N, i, j);
-    n = ld3(f, N, i, j + 1);
-  }
-  __device__ __forceinline__ void advance(const T* f, int N, int i, int j) {  // j: new centre row
-    s = m;
-    m = n;
-    n = ld3(f, N, i, j + 1);
-  }
-  __device__ __forceinline__ St9<T> st() const { return st9(s, m, n); }
-};
-
 // Arakawa J_A(a, b) times 12 d^2 (the mean of J++, J+x, Jx+ without its scale)
 template <typename T>
 __device__ __forceinline__ T arakawa12(const St9<T>& a, const St9<T>& b) {
@@ -499,117 +458,206 @@ struct StencilConsts {
   double fk_d;   // forcing wavenumber * d
 };
 
-// Stencil kernels: thread (x = i, rows j0 .. j0 + JB - 1) slides a three-row
-// window along y, so each field costs three loads per point instead of nine.
+// Stencil kernels: a block of 256 threads owns a tile of TX x 16 points of
+// one field (TX = min(N, 64)); every field read through the nine-point stencil
+// is staged with its one-point periodic halo in shared memory, and the
+// pointwise operands are loaded into registers before the barrier, so all of a
+// block's global loads are in flight at once.
+constexpr int kTileY = 16, kTileThreads = 256;
+
+template <int TX>
+struct TileGeom {
+  static constexpr int W = TX + 2, SIZE = W * (kTileY + 2);
+  static constexpr int P = TX * kTileY / kTileThreads;  // points per thread
+  static constexpr int RSTEP = kTileThreads / TX;       // row step between a thread's points
+};
+
+// Asynchronous element copy global -> shared (4 or 8 bytes, through L1).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+}
+
+// tile (jj, ii) <- f[(j0 - 1 + jj) mod N][(i0 - 1 + ii) mod N], issued as
+// asynchronous copies (all of a block's copies are in flight together);
+// tile_wait() completes them and synchronizes the block.
+template <typename T, int TX>
+__device__ __forceinline__ void tile_load(T* sm, const T* __restrict__ f, int N, int i0, int j0) {
+  using TG = TileGeom<TX>;
+  constexpr int IT = (TG::SIZE + kTileThreads - 1) / kTileThreads;
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int e = it * kTileThreads + threadIdx.x;
+    if (e < TG::SIZE) {
+      const int jj = e / TG::W, ii = e - jj * TG::W;
+      cp_async_elem(sm + e, f + (size_t)((j0 - 1 + jj) & (N - 1)) * N + ((i0 - 1 + ii) & (N - 1)));
+    }
+  }
+}
+__device__ __forceinline__ void tile_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+}
+
+// nine-point neighbourhood of interior tile point (ty, tx); n = row j + 1, e = column i + 1
+template <typename T, int TX>
+__device__ __forceinline__ St9<T> tile_st9(const T* sm, int ty, int tx) {
+  constexpr int W = TileGeom<TX>::W;
+  const T* c = sm + (ty + 1) * W + (tx + 1);
+  St9<T> v;
+  v.c = c[0]; v.e = c[1]; v.w = c[-1];
+  v.n = c[W]; v.s = c[-W];
+  v.ne = c[W + 1]; v.nw = c[W - 1]; v.se = c[-W + 1]; v.sw = c[-W - 1];
+  return v;
+}
 
 // FWD stage: f = -J_A(psi, X_s) + nu Lap X_s + F; acc += b_s f; next = x + h a_s f
 // (s = 3: x += h acc). Single field.
-template <typename T>
-__global__ void bve_fwd_stage_kernel(int N, int JB, StencilConsts sc, int s, T h, const T* __restrict__ X,
-                                     const T* __restrict__ psi, T* acc, T* x, T* next) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * JB;
-  if (i >= N || j0 >= N) return;
-  Win<T> q, ps;
-  q.init(X, N, i, j0);
-  ps.init(psi, N, i, j0);
-  for (int jj = 0; jj < JB; ++jj) {
-    const int j = j0 + jj;
-    if (jj) { q.advance(X, N, i, j); ps.advance(psi, N, i, j); }
-    St9<T> qq = q.st(), pp = ps.st();
+template <typename T, int TX>
+__global__ void __launch_bounds__(kTileThreads) bve_fwd_stage_kernel(int N, StencilConsts sc, int s, T h,
+                                                                     const T* __restrict__ X,
+                                                                     const T* __restrict__ psi, T* acc,
+                                                                     T* x, T* next) {
+  using TG = TileGeom<TX>;
+  __shared__ T sq[TG::SIZE], sp[TG::SIZE];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * kTileY;
+  const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
+  T a_r[TG::P], x_r[TG::P];
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    const size_t g = (size_t)(j0 + ty0 + r * TG::RSTEP) * N + i0 + tx;
+    a_r[r] = s == 0 ? (T)0 : acc[g];
+    x_r[r] = x[g];
+  }
+  tile_load<T, TX>(sq, X, N, i0, j0);
+  tile_load<T, TX>(sp, psi, N, i0, j0);
+  tile_wait();
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    const int ty = ty0 + r * TG::RSTEP, j = j0 + ty;
+    St9<T> qq = tile_st9<T, TX>(sq, ty, tx), pp = tile_st9<T, TX>(sp, ty, tx);
     T f = -(T)sc.c12 * arakawa12(pp, qq) + (T)sc.nudd * lap5(qq) + (T)(sc.famp * sin(sc.fk_d * j));
-    size_t g = (size_t)j * N + i;
-    T a = (s == 0 ? (T)0 : acc[g]) + (T)kBveB[s] * f;
+    const size_t g = (size_t)j * N + i0 + tx;
+    T a = a_r[r] + (T)kBveB[s] * f;
     if (s < 3) {
       acc[g] = a;
-      next[g] = x[g] + h * (T)kBveA[s] * f;
+      next[g] = x_r[r] + h * (T)kBveA[s] * f;
     } else {
-      x[g] = x[g] + h * a;
+      x[g] = x_r[r] + h * a;
     }
   }
 }
 
-// TLM stage over k directions (base q_s, psi_s shared)
-template <typename T>
-__global__ void bve_tlm_stage_kernel(int N, int JB, StencilConsts sc, int s, T h, const T* __restrict__ qb,
-                                     const T* __restrict__ pb, const T* __restrict__ cur,
-                                     const T* __restrict__ dpsi, T* acc, T* dx, T* next, size_t ld) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * JB;
-  if (i >= N || j0 >= N) return;
+// TLM stage over k directions (base q_s, psi_s shared; direction = blockIdx.z):
+// dk = -J_A(dpsi, q_s) - J_A(psi_s, dq) + nu Lap dq; acc += b_s dk;
+// next = dx + h a_s dk (s = 3: dx += h acc).
+template <typename T, int TX>
+__global__ void __launch_bounds__(kTileThreads) bve_tlm_stage_kernel(int N, StencilConsts sc, int s, T h,
+                                                                     const T* __restrict__ qb,
+                                                                     const T* __restrict__ pb,
+                                                                     const T* __restrict__ cur,
+                                                                     const T* __restrict__ dpsi, T* acc,
+                                                                     T* dx, T* next, size_t ld) {
+  using TG = TileGeom<TX>;
+  __shared__ T sq[TG::SIZE], sp[TG::SIZE], sd[TG::SIZE], sdp[TG::SIZE];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * kTileY;
+  const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
   const size_t off = (size_t)blockIdx.z * ld;
-  const T* cu = cur + off;
-  const T* dp = dpsi + off;
-  Win<T> q, ps, d, dpw;
-  q.init(qb, N, i, j0);
-  ps.init(pb, N, i, j0);
-  d.init(cu, N, i, j0);
-  dpw.init(dp, N, i, j0);
+  T a_r[TG::P], x_r[TG::P];
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    const size_t g = off + (size_t)(j0 + ty0 + r * TG::RSTEP) * N + i0 + tx;
+    a_r[r] = s == 0 ? (T)0 : acc[g];
+    x_r[r] = dx[g];
+  }
+  tile_load<T, TX>(sd, cur + off, N, i0, j0);
+  tile_load<T, TX>(sdp, dpsi + off, N, i0, j0);
+  tile_load<T, TX>(sq, qb, N, i0, j0);
+  tile_load<T, TX>(sp, pb, N, i0, j0);
+  tile_wait();
   const T bs = (T)kBveB[s];
   const T ha = (s < 3) ? h * (T)kBveA[s] : (T)0;
-  for (int jj = 0; jj < JB; ++jj) {
-    const int j = j0 + jj;
-    if (jj) { q.advance(qb, N, i, j); ps.advance(pb, N, i, j); d.advance(cu, N, i, j); dpw.advance(dp, N, i, j); }
-    St9<T> qq = q.st(), pp = ps.st(), dd = d.st(), ddp = dpw.st();
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    const int ty = ty0 + r * TG::RSTEP;
+    St9<T> qq = tile_st9<T, TX>(sq, ty, tx), pp = tile_st9<T, TX>(sp, ty, tx);
+    St9<T> dd = tile_st9<T, TX>(sd, ty, tx), ddp = tile_st9<T, TX>(sdp, ty, tx);
     T dk = -(T)sc.c12 * (arakawa12(ddp, qq) + arakawa12(pp, dd)) + (T)sc.nudd * lap5(dd);
-    size_t g = off + (size_t)j * N + i;
-    T a = (s == 0 ? (T)0 : acc[g]) + bs * dk;
+    const size_t g = off + (size_t)(j0 + ty) * N + i0 + tx;
+    T a = a_r[r] + bs * dk;
     if (s < 3) {
       acc[g] = a;
-      next[g] = dx[g] + ha * dk;
+      next[g] = x_r[r] + ha * dk;
     } else {
-      dx[g] = dx[g] + h * a;
+      dx[g] = x_r[r] + h * a;
     }
   }
 }
 
 // ADJ: T1 = J_A(q_s, kappa)
-template <typename T>
-__global__ void bve_adj_jac_kernel(int N, int JB, StencilConsts sc, const T* __restrict__ qb,
-                                   const T* __restrict__ kap, T* t1, size_t ld) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * JB;
-  if (i >= N || j0 >= N) return;
+template <typename T, int TX>
+__global__ void __launch_bounds__(kTileThreads) bve_adj_jac_kernel(int N, StencilConsts sc,
+                                                                   const T* __restrict__ qb,
+                                                                   const T* __restrict__ kap, T* t1,
+                                                                   size_t ld) {
+  using TG = TileGeom<TX>;
+  __shared__ T sq[TG::SIZE], sk[TG::SIZE];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * kTileY;
+  const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
   const size_t off = (size_t)blockIdx.z * ld;
-  const T* kp = kap + off;
-  Win<T> q, kk;
-  q.init(qb, N, i, j0);
-  kk.init(kp, N, i, j0);
-  for (int jj = 0; jj < JB; ++jj) {
-    const int j = j0 + jj;
-    if (jj) { q.advance(qb, N, i, j); kk.advance(kp, N, i, j); }
-    t1[off + (size_t)j * N + i] = (T)sc.c12 * arakawa12(q.st(), kk.st());
+  tile_load<T, TX>(sk, kap + off, N, i0, j0);
+  tile_load<T, TX>(sq, qb, N, i0, j0);
+  tile_wait();
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    const int ty = ty0 + r * TG::RSTEP;
+    t1[off + (size_t)(j0 + ty) * N + i0 + tx] =
+        (T)sc.c12 * arakawa12(tile_st9<T, TX>(sq, ty, tx), tile_st9<T, TX>(sk, ty, tx));
   }
 }
 
 // ADJ stage: theta = -T2 + J_A(psi_s, kappa) + nu Lap kappa; th += theta;
 // s > 0: kappa_{s-1} = h b_{s-1} lam + h a_{s-1} theta; s = 0: lam += th
-template <typename T>
-__global__ void bve_adj_stage_kernel(int N, int JB, StencilConsts sc, int s, T h, const T* __restrict__ pb,
-                                     const T* __restrict__ kap, const T* __restrict__ t2, T* th,
-                                     T* lam, T* knext, size_t ld) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * JB;
-  if (i >= N || j0 >= N) return;
+template <typename T, int TX>
+__global__ void __launch_bounds__(kTileThreads) bve_adj_stage_kernel(int N, StencilConsts sc, int s, T h,
+                                                                     const T* __restrict__ pb,
+                                                                     const T* __restrict__ kap,
+                                                                     const T* __restrict__ t2, T* th,
+                                                                     T* lam, T* knext, size_t ld) {
+  using TG = TileGeom<TX>;
+  __shared__ T sp[TG::SIZE], sk[TG::SIZE];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * kTileY;
+  const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
   const size_t off = (size_t)blockIdx.z * ld;
-  const T* kp = kap + off;
-  Win<T> ps, kk;
-  ps.init(pb, N, i, j0);
-  kk.init(kp, N, i, j0);
+  T t2_r[TG::P], th_r[TG::P], l_r[TG::P];
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    const size_t g = off + (size_t)(j0 + ty0 + r * TG::RSTEP) * N + i0 + tx;
+    t2_r[r] = t2[g];
+    th_r[r] = s == 3 ? (T)0 : th[g];
+    l_r[r] = lam[g];
+  }
+  tile_load<T, TX>(sk, kap + off, N, i0, j0);
+  tile_load<T, TX>(sp, pb, N, i0, j0);
+  tile_wait();
   const T hb = (s > 0) ? h * (T)kBveB[s - 1] : (T)0;
   const T ha = (s > 0) ? h * (T)kBveA[s - 1] : (T)0;
-  for (int jj = 0; jj < JB; ++jj) {
-    const int j = j0 + jj;
-    if (jj) { ps.advance(pb, N, i, j); kk.advance(kp, N, i, j); }
-    St9<T> k9 = kk.st();
-    size_t g = off + (size_t)j * N + i;
-    T theta = -t2[g] + (T)sc.c12 * arakawa12(ps.st(), k9) + (T)sc.nudd * lap5(k9);
-    T a = (s == 3 ? (T)0 : th[g]) + theta;
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    const int ty = ty0 + r * TG::RSTEP;
+    St9<T> k9 = tile_st9<T, TX>(sk, ty, tx);
+    const size_t g = off + (size_t)(j0 + ty) * N + i0 + tx;
+    T theta = -t2_r[r] + (T)sc.c12 * arakawa12(tile_st9<T, TX>(sp, ty, tx), k9) + (T)sc.nudd * lap5(k9);
+    T a = th_r[r] + theta;
     if (s > 0) {
       th[g] = a;
-      knext[g] = hb * lam[g] + ha * theta;
+      knext[g] = hb * l_r[r] + ha * theta;
     } else {
-      lam[g] = lam[g] + a;
+      lam[g] = l_r[r] + a;
     }
   }
 }
@@ -770,10 +818,16 @@ static StencilConsts consts(const BveGeom& g) {
   return c;
 }
 
-// Rows per thread of the stencil kernels and the launch grid for k fields
-// (blocks of 32 x 8 threads, each thread JB rows).
-static int stencil_jb(int N) { return N >= 64 ? 8 : 2; }
-static dim3 sgrid(int N, int k) { return dim3(div_up(N, 32), div_up(N / stencil_jb(N), 8), k); }
+// Launch grid of the tiled stencil kernels for k fields, and the dispatch on
+// the tile width TX = min(N, 64).
+static dim3 sgrid(int N, int k) { return dim3(N / std::min(N, 64), N / kTileY, k); }
+#define SC4_STENCIL(N, KERNEL, T, ...)                                                        \
+  do {                                                                                        \
+    if ((N) >= 64) KERNEL<T, 64><<<sgrid(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);         \
+    else if ((N) == 32) KERNEL<T, 32><<<sgrid(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);    \
+    else KERNEL<T, 16><<<sgrid(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);                   \
+    SC4_LAUNCH_CHECK();                                                                       \
+  } while (0)
 
 template <typename T>
 static int scale_fields(size_t total, T a, const T* x, T* y, cudaStream_t st) {
@@ -831,7 +885,7 @@ static int fwd_steps(const BveGeom& g, void* ws_fwd, int t0, int t1, double* q64
   double* ptmp = acc + 3 * n;
   void* cbuf = ptmp + n;
   StencilConsts sc = consts(g);
-  const dim3 grid = sgrid(N, 1), blk(32, 8);
+  const int kz = 1;
   for (int t = t0; t < t1; ++t) {
     SC4_TRY(fwd_obs(g, t, x, y, d_out, obs_out, st));
     if (save_ckpt && g.ckpt_every > 0 && t % g.ckpt_every == 0)
@@ -848,8 +902,7 @@ static int fwd_steps(const BveGeom& g, void* ws_fwd, int t0, int t1, double* q64
         SC4_TRY(d2f(n, Xs, q32 + row, st));
         SC4_TRY(d2f(n, ps, p32 + row, st));
       }
-      bve_fwd_stage_kernel<double><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, g.h, Xs, ps, acc, x, nxt);
-      SC4_LAUNCH_CHECK();
+      SC4_STENCIL(N, bve_fwd_stage_kernel, double, N, sc, s, g.h, Xs, ps, acc, x, nxt);
     }
   }
   return SC4DVAR_OK;
@@ -924,7 +977,7 @@ int bve_tlm(const BveGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* 
   for (int c = 0; c < k; ++c)
     SC4_CUDA(cudaMemcpyAsync(dx + (size_t)c * n, U0 + (size_t)c * ldu, n * sizeof(T),
                              cudaMemcpyDeviceToDevice, st));
-  const dim3 grid = sgrid(N, k), blk(32, 8);
+  const int kz = k;
   auto gather = [&](int t) -> int {
     int oi = g.obs_of_step_h[t];
     if (oi >= 0) {
@@ -946,9 +999,8 @@ int bve_tlm(const BveGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* 
         size_t row = (size_t)(4 * (t - base) + s) * n;
         SC4_TRY(fft2_apply<T, T, T, T>(g, k, cur, (int)n, dpsi, (int)n, (const T*)nullptr, 0, g.poisson,
                                        cbuf, st));
-        bve_tlm_stage_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, (T)g.h, qbase<T>(g) + row,
-                                                      pbase<T>(g) + row, cur, dpsi, acc, dx, nxt, n);
-        SC4_LAUNCH_CHECK();
+        SC4_STENCIL(N, bve_tlm_stage_kernel, T, N, sc, s, (T)g.h, qbase<T>(g) + row, pbase<T>(g) + row,
+                    cur, dpsi, acc, dx, nxt, n);
       }
     }
   }
@@ -969,7 +1021,7 @@ int bve_adj(const BveGeom& g, const T* W, int ldw, int k, T* Out, int ldo, void*
   StencilConsts sc = consts(g);
   const T inv_sigma = (T)(1.0 / g.sigma);
   SC4_CUDA(cudaMemsetAsync(lam, 0, nk * sizeof(T), st));
-  const dim3 grid = sgrid(N, k), blk(32, 8);
+  const int kz = k;
   const T h = (T)g.h;
   for (int j = n_segments(g) - 1; j >= 0; --j) {
     const Segment sg = segment_of(g, j);
@@ -987,13 +1039,11 @@ int bve_adj(const BveGeom& g, const T* W, int ldw, int k, T* Out, int ldo, void*
         const T* kap = K[(3 - s) & 1];
         T* knext = K[(4 - s) & 1];
         size_t row = (size_t)(4 * (t - 1 - base) + s) * n;
-        bve_adj_jac_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, qbase<T>(g) + row, kap, t12, n);
-        SC4_LAUNCH_CHECK();
+        SC4_STENCIL(N, bve_adj_jac_kernel, T, N, sc, qbase<T>(g) + row, kap, t12, n);
         SC4_TRY(fft2_apply<T, T, T, T>(g, k, t12, (int)n, t12, (int)n, (const T*)nullptr, 0, g.poisson,
                                        cbuf, st));
-        bve_adj_stage_kernel<T><<<grid, blk, 0, st>>>(N, stencil_jb(N), sc, s, h, pbase<T>(g) + row, kap,
-                                                      t12, th, lam, s > 0 ? knext : nullptr, n);
-        SC4_LAUNCH_CHECK();
+        SC4_STENCIL(N, bve_adj_stage_kernel, T, N, sc, s, h, pbase<T>(g) + row, kap, t12, th, lam,
+                    s > 0 ? knext : nullptr, n);
       }
     }
   }
