@@ -458,21 +458,26 @@ struct StencilConsts {
   double fk_d;   // forcing wavenumber * d
 };
 
-// Stencil kernels: a block of 256 threads owns a tile of TX x 16 points of
-// one field (TX = min(N, 64)); every field read through the nine-point stencil
-// is staged with its one-point periodic halo in shared memory, and the
-// pointwise operands are loaded into registers before the barrier, so all of a
-// block's global loads are in flight at once.
-constexpr int kTileY = 16, kTileThreads = 256;
+// Stencil kernels: a block of 256 threads owns a tile of TX x TY points of
+// one field (TX = min(N, 64); TY = min(N, 32) for FP32, min(N, 16) for FP64);
+// every field read through the nine-point stencil is staged with its one-point
+// periodic halo in shared memory by asynchronous copies (16-byte vectors for
+// the tile interior), and the pointwise operands are loaded into registers
+// before the wait, so all of a block's global loads are in flight at once.
+constexpr int kTileThreads = 256;
 
-template <int TX>
+template <typename T, int TX>
 struct TileGeom {
-  static constexpr int W = TX + 2, SIZE = W * (kTileY + 2);
-  static constexpr int P = TX * kTileY / kTileThreads;  // points per thread
-  static constexpr int RSTEP = kTileThreads / TX;       // row step between a thread's points
+  static constexpr int V = 16 / (int)sizeof(T);              // elements per 16-byte vector
+  static constexpr int TY = sizeof(T) == 4 ? (TX < 32 ? TX : 32) : (TX < 16 ? TX : 16);
+  static constexpr int O = V;                                // column of the first interior point
+  static constexpr int W = TX + 2 * V;                       // row stride (16-byte multiple)
+  static constexpr int SIZE = W * (TY + 2);
+  static constexpr int P = TX * TY / kTileThreads;           // points per thread
+  static constexpr int BANDS = kTileThreads / TX;            // row bands per tile (P rows each)
+  static constexpr int UPR = TX / V + 2;                     // copies per row: vectors + two halos
 };
 
-// Asynchronous element copy global -> shared (4 or 8 bytes, through L1).
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -481,20 +486,30 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
 }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
 
-// tile (jj, ii) <- f[(j0 - 1 + jj) mod N][(i0 - 1 + ii) mod N], issued as
-// asynchronous copies (all of a block's copies are in flight together);
-// tile_wait() completes them and synchronizes the block.
+// tile row jj <- f row (j0 - 1 + jj) mod N: interior columns i0 .. i0 + TX - 1
+// at O .. O + TX - 1 (16-byte copies; i0 and N are multiples of TX, so both
+// sides are 16-byte aligned), halos (i0 - 1) mod N at O - 1 and (i0 + TX) mod N
+// at O + TX. tile_wait() completes the copies and synchronizes the block.
 template <typename T, int TX>
 __device__ __forceinline__ void tile_load(T* sm, const T* __restrict__ f, int N, int i0, int j0) {
-  using TG = TileGeom<TX>;
-  constexpr int IT = (TG::SIZE + kTileThreads - 1) / kTileThreads;
+  using TG = TileGeom<T, TX>;
+  constexpr int UNITS = TG::UPR * (TG::TY + 2);
+  constexpr int IT = (UNITS + kTileThreads - 1) / kTileThreads;
 #pragma unroll
   for (int it = 0; it < IT; ++it) {
-    const int e = it * kTileThreads + threadIdx.x;
-    if (e < TG::SIZE) {
-      const int jj = e / TG::W, ii = e - jj * TG::W;
-      cp_async_elem(sm + e, f + (size_t)((j0 - 1 + jj) & (N - 1)) * N + ((i0 - 1 + ii) & (N - 1)));
+    const int u = it * kTileThreads + threadIdx.x;
+    if (u < UNITS) {
+      const int jj = u / TG::UPR, c = u - jj * TG::UPR;
+      const T* row = f + (size_t)((j0 - 1 + jj) & (N - 1)) * N;
+      T* srow = sm + jj * TG::W;
+      if (c < TX / TG::V) cp_async16(srow + TG::O + c * TG::V, row + i0 + c * TG::V);
+      else if (c == TX / TG::V) cp_async_elem(srow + TG::O - 1, row + ((i0 - 1) & (N - 1)));
+      else cp_async_elem(srow + TG::O + TX, row + ((i0 + TX) & (N - 1)));
     }
   }
 }
@@ -503,17 +518,35 @@ __device__ __forceinline__ void tile_wait() {
   __syncthreads();
 }
 
-// nine-point neighbourhood of interior tile point (ty, tx); n = row j + 1, e = column i + 1
+// Three-row register window over a staged tile: a thread owns P consecutive
+// interior rows of one column and slides down them, reading three values of
+// the new row per step. n = row j + 1, e = column i + 1.
 template <typename T, int TX>
-__device__ __forceinline__ St9<T> tile_st9(const T* sm, int ty, int tx) {
-  constexpr int W = TileGeom<TX>::W;
-  const T* c = sm + (ty + 1) * W + (tx + 1);
-  St9<T> v;
-  v.c = c[0]; v.e = c[1]; v.w = c[-1];
-  v.n = c[W]; v.s = c[-W];
-  v.ne = c[W + 1]; v.nw = c[W - 1]; v.se = c[-W + 1]; v.sw = c[-W - 1];
-  return v;
-}
+struct TileWin {
+  const T* col;     // the thread's column in tile row 0
+  T sw, sc, se, mw, mc, me, nw, nc, ne;
+  __device__ __forceinline__ void init(const T* sm, int tx, int ty) {  // ty: first interior row
+    col = sm + TileGeom<T, TX>::O + tx;
+    ld(ty, sw, sc, se);
+    ld(ty + 1, mw, mc, me);
+    ld(ty + 2, nw, nc, ne);
+  }
+  __device__ __forceinline__ void ld(int trow, T& w, T& c, T& e) const {
+    const T* p = col + trow * TileGeom<T, TX>::W;
+    w = p[-1]; c = p[0]; e = p[1];
+  }
+  __device__ __forceinline__ void advance(int ty) {  // ty: the new centre interior row
+    sw = mw; sc = mc; se = me;
+    mw = nw; mc = nc; me = ne;
+    ld(ty + 2, nw, nc, ne);
+  }
+  __device__ __forceinline__ St9<T> st() const {
+    St9<T> v;
+    v.c = mc; v.e = me; v.w = mw;
+    v.n = nc; v.s = sc; v.ne = ne; v.nw = nw; v.se = se; v.sw = sw;
+    return v;
+  }
+};
 
 // FWD stage: f = -J_A(psi, X_s) + nu Lap X_s + F; acc += b_s f; next = x + h a_s f
 // (s = 3: x += h acc). Single field.
@@ -522,24 +555,28 @@ __global__ void __launch_bounds__(kTileThreads) bve_fwd_stage_kernel(int N, Sten
                                                                      const T* __restrict__ X,
                                                                      const T* __restrict__ psi, T* acc,
                                                                      T* x, T* next) {
-  using TG = TileGeom<TX>;
-  __shared__ T sq[TG::SIZE], sp[TG::SIZE];
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * kTileY;
-  const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
+  using TG = TileGeom<T, TX>;
+  __shared__ __align__(16) T sq[TG::SIZE], sp[TG::SIZE];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TG::TY;
+  const int tx = threadIdx.x % TX, ty0 = (threadIdx.x / TX) * TG::P;
   T a_r[TG::P], x_r[TG::P];
 #pragma unroll
   for (int r = 0; r < TG::P; ++r) {
-    const size_t g = (size_t)(j0 + ty0 + r * TG::RSTEP) * N + i0 + tx;
+    const size_t g = (size_t)(j0 + ty0 + r) * N + i0 + tx;
     a_r[r] = s == 0 ? (T)0 : acc[g];
     x_r[r] = x[g];
   }
   tile_load<T, TX>(sq, X, N, i0, j0);
   tile_load<T, TX>(sp, psi, N, i0, j0);
   tile_wait();
+  TileWin<T, TX> q, ps;
+  q.init(sq, tx, ty0);
+  ps.init(sp, tx, ty0);
 #pragma unroll
   for (int r = 0; r < TG::P; ++r) {
-    const int ty = ty0 + r * TG::RSTEP, j = j0 + ty;
-    St9<T> qq = tile_st9<T, TX>(sq, ty, tx), pp = tile_st9<T, TX>(sp, ty, tx);
+    const int j = j0 + ty0 + r;
+    if (r) { q.advance(ty0 + r); ps.advance(ty0 + r); }
+    St9<T> qq = q.st(), pp = ps.st();
     T f = -(T)sc.c12 * arakawa12(pp, qq) + (T)sc.nudd * lap5(qq) + (T)(sc.famp * sin(sc.fk_d * j));
     const size_t g = (size_t)j * N + i0 + tx;
     T a = a_r[r] + (T)kBveB[s] * f;
@@ -562,15 +599,15 @@ __global__ void __launch_bounds__(kTileThreads) bve_tlm_stage_kernel(int N, Sten
                                                                      const T* __restrict__ cur,
                                                                      const T* __restrict__ dpsi, T* acc,
                                                                      T* dx, T* next, size_t ld) {
-  using TG = TileGeom<TX>;
-  __shared__ T sq[TG::SIZE], sp[TG::SIZE], sd[TG::SIZE], sdp[TG::SIZE];
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * kTileY;
-  const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
+  using TG = TileGeom<T, TX>;
+  __shared__ __align__(16) T sq[TG::SIZE], sp[TG::SIZE], sd[TG::SIZE], sdp[TG::SIZE];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TG::TY;
+  const int tx = threadIdx.x % TX, ty0 = (threadIdx.x / TX) * TG::P;
   const size_t off = (size_t)blockIdx.z * ld;
   T a_r[TG::P], x_r[TG::P];
 #pragma unroll
   for (int r = 0; r < TG::P; ++r) {
-    const size_t g = off + (size_t)(j0 + ty0 + r * TG::RSTEP) * N + i0 + tx;
+    const size_t g = off + (size_t)(j0 + ty0 + r) * N + i0 + tx;
     a_r[r] = s == 0 ? (T)0 : acc[g];
     x_r[r] = dx[g];
   }
@@ -581,13 +618,17 @@ __global__ void __launch_bounds__(kTileThreads) bve_tlm_stage_kernel(int N, Sten
   tile_wait();
   const T bs = (T)kBveB[s];
   const T ha = (s < 3) ? h * (T)kBveA[s] : (T)0;
+  TileWin<T, TX> q, ps, d, dp;
+  q.init(sq, tx, ty0);
+  ps.init(sp, tx, ty0);
+  d.init(sd, tx, ty0);
+  dp.init(sdp, tx, ty0);
 #pragma unroll
   for (int r = 0; r < TG::P; ++r) {
-    const int ty = ty0 + r * TG::RSTEP;
-    St9<T> qq = tile_st9<T, TX>(sq, ty, tx), pp = tile_st9<T, TX>(sp, ty, tx);
-    St9<T> dd = tile_st9<T, TX>(sd, ty, tx), ddp = tile_st9<T, TX>(sdp, ty, tx);
+    if (r) { q.advance(ty0 + r); ps.advance(ty0 + r); d.advance(ty0 + r); dp.advance(ty0 + r); }
+    St9<T> qq = q.st(), pp = ps.st(), dd = d.st(), ddp = dp.st();
     T dk = -(T)sc.c12 * (arakawa12(ddp, qq) + arakawa12(pp, dd)) + (T)sc.nudd * lap5(dd);
-    const size_t g = off + (size_t)(j0 + ty) * N + i0 + tx;
+    const size_t g = off + (size_t)(j0 + ty0 + r) * N + i0 + tx;
     T a = a_r[r] + bs * dk;
     if (s < 3) {
       acc[g] = a;
@@ -604,19 +645,21 @@ __global__ void __launch_bounds__(kTileThreads) bve_adj_jac_kernel(int N, Stenci
                                                                    const T* __restrict__ qb,
                                                                    const T* __restrict__ kap, T* t1,
                                                                    size_t ld) {
-  using TG = TileGeom<TX>;
-  __shared__ T sq[TG::SIZE], sk[TG::SIZE];
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * kTileY;
-  const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
+  using TG = TileGeom<T, TX>;
+  __shared__ __align__(16) T sq[TG::SIZE], sk[TG::SIZE];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TG::TY;
+  const int tx = threadIdx.x % TX, ty0 = (threadIdx.x / TX) * TG::P;
   const size_t off = (size_t)blockIdx.z * ld;
   tile_load<T, TX>(sk, kap + off, N, i0, j0);
   tile_load<T, TX>(sq, qb, N, i0, j0);
   tile_wait();
+  TileWin<T, TX> q, kk;
+  q.init(sq, tx, ty0);
+  kk.init(sk, tx, ty0);
 #pragma unroll
   for (int r = 0; r < TG::P; ++r) {
-    const int ty = ty0 + r * TG::RSTEP;
-    t1[off + (size_t)(j0 + ty) * N + i0 + tx] =
-        (T)sc.c12 * arakawa12(tile_st9<T, TX>(sq, ty, tx), tile_st9<T, TX>(sk, ty, tx));
+    if (r) { q.advance(ty0 + r); kk.advance(ty0 + r); }
+    t1[off + (size_t)(j0 + ty0 + r) * N + i0 + tx] = (T)sc.c12 * arakawa12(q.st(), kk.st());
   }
 }
 
@@ -628,15 +671,15 @@ __global__ void __launch_bounds__(kTileThreads) bve_adj_stage_kernel(int N, Sten
                                                                      const T* __restrict__ kap,
                                                                      const T* __restrict__ t2, T* th,
                                                                      T* lam, T* knext, size_t ld) {
-  using TG = TileGeom<TX>;
-  __shared__ T sp[TG::SIZE], sk[TG::SIZE];
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * kTileY;
-  const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
+  using TG = TileGeom<T, TX>;
+  __shared__ __align__(16) T sp[TG::SIZE], sk[TG::SIZE];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TG::TY;
+  const int tx = threadIdx.x % TX, ty0 = (threadIdx.x / TX) * TG::P;
   const size_t off = (size_t)blockIdx.z * ld;
   T t2_r[TG::P], th_r[TG::P], l_r[TG::P];
 #pragma unroll
   for (int r = 0; r < TG::P; ++r) {
-    const size_t g = off + (size_t)(j0 + ty0 + r * TG::RSTEP) * N + i0 + tx;
+    const size_t g = off + (size_t)(j0 + ty0 + r) * N + i0 + tx;
     t2_r[r] = t2[g];
     th_r[r] = s == 3 ? (T)0 : th[g];
     l_r[r] = lam[g];
@@ -646,12 +689,15 @@ __global__ void __launch_bounds__(kTileThreads) bve_adj_stage_kernel(int N, Sten
   tile_wait();
   const T hb = (s > 0) ? h * (T)kBveB[s - 1] : (T)0;
   const T ha = (s > 0) ? h * (T)kBveA[s - 1] : (T)0;
+  TileWin<T, TX> ps, kk;
+  ps.init(sp, tx, ty0);
+  kk.init(sk, tx, ty0);
 #pragma unroll
   for (int r = 0; r < TG::P; ++r) {
-    const int ty = ty0 + r * TG::RSTEP;
-    St9<T> k9 = tile_st9<T, TX>(sk, ty, tx);
-    const size_t g = off + (size_t)(j0 + ty) * N + i0 + tx;
-    T theta = -t2_r[r] + (T)sc.c12 * arakawa12(tile_st9<T, TX>(sp, ty, tx), k9) + (T)sc.nudd * lap5(k9);
+    if (r) { ps.advance(ty0 + r); kk.advance(ty0 + r); }
+    St9<T> k9 = kk.st();
+    const size_t g = off + (size_t)(j0 + ty0 + r) * N + i0 + tx;
+    T theta = -t2_r[r] + (T)sc.c12 * arakawa12(ps.st(), k9) + (T)sc.nudd * lap5(k9);
     T a = th_r[r] + theta;
     if (s > 0) {
       th[g] = a;
@@ -820,13 +866,14 @@ static StencilConsts consts(const BveGeom& g) {
 
 // Launch grid of the tiled stencil kernels for k fields, and the dispatch on
 // the tile width TX = min(N, 64).
-static dim3 sgrid(int N, int k) { return dim3(N / std::min(N, 64), N / kTileY, k); }
-#define SC4_STENCIL(N, KERNEL, T, ...)                                                        \
-  do {                                                                                        \
-    if ((N) >= 64) KERNEL<T, 64><<<sgrid(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);         \
-    else if ((N) == 32) KERNEL<T, 32><<<sgrid(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);    \
-    else KERNEL<T, 16><<<sgrid(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);                   \
-    SC4_LAUNCH_CHECK();                                                                       \
+template <typename T, int TX>
+static dim3 sgrid(int N, int k) { return dim3(N / TX, N / TileGeom<T, TX>::TY, k); }
+#define SC4_STENCIL(N, KERNEL, T, ...)                                                          \
+  do {                                                                                          \
+    if ((N) >= 64) KERNEL<T, 64><<<sgrid<T, 64>(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);    \
+    else if ((N) == 32) KERNEL<T, 32><<<sgrid<T, 32>(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__); \
+    else KERNEL<T, 16><<<sgrid<T, 16>(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);              \
+    SC4_LAUNCH_CHECK();                                                                         \
   } while (0)
 
 template <typename T>
