@@ -545,13 +545,17 @@ def profile_case():
     print("profile case done")
 
 
-def profile_case_bve():
-    """One FP32 TLM block and one FP32 ADJ block (k = 256) of the 256 x 256
-    vorticity workload on its first 20 RK4 steps (two observation times)."""
+def profile_case_bve(name="bve_n256"):
+    """One FP32 TLM block and one FP32 ADJ block of a vorticity workload on its
+    first RK4 steps: 256^2 (k = 256) 20 steps; 1024^2 (k = 512) 16 steps with 4
+    checkpoints (segments of 4 steps)."""
     import torch
     import paper_2401_15758_gb300 as g
     import sc4dvar_inputs as si
-    wl = si.bve_workload("bve_n256", n_steps=20)
+    if name == "bve_n1024":
+        wl = si.bve_workload(name, n_steps=16, n_checkpoints=4)
+    else:
+        wl = si.bve_workload(name, n_steps=20)
     d = si.bve_draws(wl)
     prob = g.Problem.from_bve_workload(wl, d)
     prob.set_background(torch.tensor(d["x_true0"], device="cuda"))
@@ -567,8 +571,8 @@ def profile_case_bve():
 def main():
     args = parse()
     if args.profile:
-        if args.workload == "bve_n256":
-            profile_case_bve()
+        if args.workload in ("bve_n256", "bve_n1024"):
+            profile_case_bve(args.workload)
         else:
             profile_case()
         return

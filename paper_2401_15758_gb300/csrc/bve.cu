@@ -22,6 +22,7 @@
 // inverse column FFT (one pass); inverse row FFTs. Radix-2 in shared memory with
 // a per-problem twiddle table.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include "bve.cuh"
 #include "common.cuh"
@@ -278,9 +279,20 @@ __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y
 template <typename C>
 __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
 
-template <typename C, int N, int CB, int G>
-__global__ void __launch_bounds__(G * CB) wfft_cols2(C* cbuf, const typename CplxOf<C>::R* __restrict__ tab,
-                                                     const C* __restrict__ tw) {
+// w^idx v with the two trivial twiddles (idx 0: 1; idx N/4: -i forward, +i
+// inverse) applied without a multiply; where idx is a compile-time constant
+// after unrolling the branches fold away. tw[0] = 1 and tw[N/4] = -i exactly,
+// so the result equals the general product.
+template <typename C, int N>
+__device__ __forceinline__ C twmul(const C* __restrict__ tw, int idx, int dir, C v) {
+  if (idx == 0) return v;
+  if (idx == N / 4) return dir < 0 ? cmk<C>(v.y, -v.x) : cmk<C>(-v.y, v.x);
+  return cmulc(twid(tw, idx, dir), v);
+}
+
+template <typename C, int N, int CB, int G, int MINB>
+__global__ void __launch_bounds__(G * CB, MINB) wfft_cols2(C* cbuf, const typename CplxOf<C>::R* __restrict__ tab,
+                                                           const C* __restrict__ tw) {
   constexpr int R = N / G;
   static_assert(G * G <= N && R >= 2, "two-phase column split needs G^2 <= N");
   using Rl = typename CplxOf<C>::R;
@@ -316,10 +328,9 @@ __global__ void __launch_bounds__(G * CB) wfft_cols2(C* cbuf, const typename Cpl
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & h) continue;
-      C w = twid(tw, (r & (h - 1)) * (N / (2 * h)), -1);
       C u = v[r], x = v[r + h];
       v[r] = cadd(u, x);
-      v[r + h] = cmulc(w, csub(u, x));
+      v[r + h] = twmul<C, N>(tw, (r & (h - 1)) * (N / (2 * h)), -1, csub(u, x));
     }
   }
 #pragma unroll
@@ -333,8 +344,7 @@ __global__ void __launch_bounds__(G * CB) wfft_cols2(C* cbuf, const typename Cpl
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & h) continue;
-      C w = twid(tw, (r & (h - 1)) * (N / (2 * h)), +1);
-      C t = cmulc(w, v[r + h]);
+      C t = twmul<C, N>(tw, (r & (h - 1)) * (N / (2 * h)), +1, v[r + h]);
       v[r + h] = csub(v[r], t);
       v[r] = cadd(v[r], t);
     }
@@ -767,27 +777,62 @@ template <> const float2* tw_of<float2>(const BveGeom& g) { return g.tw32; }
 
 
 
-// Column-pass shape: CB columns per block (a 128-byte row segment for FP32
-// complex, 128 bytes for FP64 complex with CB = 8), G row groups, G^2 <= N.
-template <typename C>
-struct ColShape {
-  static constexpr int CB = sizeof(C) == 8 ? 16 : 8;
-};
+// Column-pass shape: CB adjacent columns per block (16 FP32 / 8 FP64 complex
+// values: a 128-byte row segment), G row groups with G^2 <= N, and a register
+// cap (MINB resident blocks). FP32 grids of 256 and more points per side take
+// one of four shapes (kColsShape below; SC4DVAR_COLS_SHAPE = 0..3 overrides
+// it as a tuning knob): 0 = 16 columns, no cap; 1 = 16 columns, <= 64
+// registers; 2 = 8 columns, no cap; 3 = 8 columns, <= 96 registers.
 constexpr int col_groups(int N) { return N >= 1024 ? 32 : N >= 256 ? 16 : N >= 64 ? 8 : 4; }
+constexpr int col_minb(int threads, int cap) {
+  return cap == 0 ? 1 : (65536 / (threads * cap) > 0 ? 65536 / (threads * cap) : 1);
+}
+static int cols_shape(int N) {
+  static const int env = [] {
+    const char* e = getenv("SC4DVAR_COLS_SHAPE");
+    return e ? atoi(e) : -1;
+  }();
+  if (env >= 0 && env <= 3) return env;
+  return 3;
+}
+
+template <typename C, int N, int CB, int CAP>
+static void launch_cols(int pairs, C* cb, const typename CplxOf<C>::R* tab, const C* tw, cudaStream_t st,
+                        int* rc) {
+  constexpr int G = col_groups(N);
+  auto kc = wfft_cols2<C, N, CB, G, col_minb(G * CB, CAP)>;
+  const size_t smc = (size_t)N * CB * sizeof(C);
+  if (cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc) != cudaSuccess) {
+    *rc = SC4DVAR_ERR_CUDA;
+    return;
+  }
+  kc<<<dim3(N / CB, pairs), G * CB, smc, st>>>(cb, tab, tw);
+}
 
 template <typename C, typename RI, typename RO, typename RZ, int RR>
 static int wfft2(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, const RZ* Z, int ldz,
                  const double* table, C* cb, cudaStream_t st) {
-  constexpr int N = RR * 32, CB = ColShape<C>::CB, G = col_groups(N);
+  constexpr int N = RR * 32;
   const int pairs = (k + 1) / 2;
-  const size_t smc = (size_t)N * CB * sizeof(C);
-  auto kc = wfft_cols2<C, N, CB, G>;
-  SC4_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
   wfft_rows_fwd<C, RI, RR><<<dim3(div_up(N, 8), pairs), 256, 0, st>>>(N, k, X, ldx, cb, tw_of<C>(g));
   SC4_LAUNCH_CHECK();
   using Rl = typename CplxOf<C>::R;
   const Rl* tab = reinterpret_cast<const Rl*>(table_brev(g, table, sizeof(Rl)));
-  kc<<<dim3(N / CB, pairs), G * CB, smc, st>>>(cb, tab, tw_of<C>(g));
+  int rc = SC4DVAR_OK;
+  if constexpr (sizeof(C) == 8 && N >= 256) {
+    switch (cols_shape(N)) {
+      case 0: launch_cols<C, N, 16, 0>(pairs, cb, tab, tw_of<C>(g), st, &rc); break;
+      case 1: launch_cols<C, N, 16, 64>(pairs, cb, tab, tw_of<C>(g), st, &rc); break;
+      case 2: launch_cols<C, N, 8, 0>(pairs, cb, tab, tw_of<C>(g), st, &rc); break;
+      default: launch_cols<C, N, 8, 96>(pairs, cb, tab, tw_of<C>(g), st, &rc); break;
+    }
+  } else {
+    launch_cols<C, N, sizeof(C) == 8 ? 16 : 8, 0>(pairs, cb, tab, tw_of<C>(g), st, &rc);
+  }
+  if (rc != SC4DVAR_OK) {
+    set_error("column pass: cudaFuncSetAttribute failed");
+    return rc;
+  }
   SC4_LAUNCH_CHECK();
   wfft_rows_inv<C, RO, RZ, RR><<<dim3(div_up(N, 8), pairs), 256, 0, st>>>(N, k, cb, Y, ldy, Z, ldz,
                                                                           tw_of<C>(g));
