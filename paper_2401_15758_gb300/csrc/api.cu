@@ -250,10 +250,10 @@ static int host_scalar(Prob* P, double* out, cudaStream_t st) {
 // ------------------------------------------------------------------ sketch helpers
 // Workspace for the dense steps of one sketch.
 struct SketchWS {
-  Buf a, b, c, g, g2, u, w, info;
+  Buf a, b, c, g, g2, u, w, info, jw;
   void release() {
     a.release(); b.release(); c.release(); g.release(); g2.release(); u.release(); w.release();
-    info.release();
+    info.release(); jw.release();
   }
 };
 
@@ -335,7 +335,8 @@ static int finalize_svd(Prob* P, int l, const T* Wt, int ldw, double nu, double 
   double* w = ws.w.as<double>();
   double* ws_ = w + l;
   SC4_TRY(gemm_tn<T, T>(n, l, l, 1.0, Wt, ldw, Wt, ldw, 0.0, G, l, st));
-  SC4_TRY(jacobi_eig(l, G, l, U, l, w, 60, 1e-15, nullptr, st));
+  SC4_TRY(ws.jw.ensure(jacobi_work_bytes(l)));
+  SC4_TRY(jacobi_eig(l, G, l, U, l, w, 60, 1e-15, ws.jw.p, nullptr, st));
   SC4_TRY(sort_desc(l, w, U, l, ws_, Us, l, st));
   std::vector<double> hw(l);
   SC4_CUDA(cudaMemcpyAsync(hw.data(), ws_, l * sizeof(double), cudaMemcpyDeviceToHost, st));

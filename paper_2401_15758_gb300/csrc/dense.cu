@@ -194,87 +194,145 @@ __global__ void trtri_lower_kernel(int l, const double* L, int ldl, double* X, i
 }
 
 // ------------------------------------------------------------------ Jacobi
-// Cyclic two-sided Jacobi for a symmetric l x l matrix A (overwritten); V gets
-// the eigenvectors, w the eigenvalues (unsorted). Round-robin order: in round r
-// of a sweep the pairs are (m-1, r) and ((r+i) mod (m-1), (r-i) mod (m-1)),
-// i = 1..m/2-1, m = l rounded up to even; all pairs of a round are disjoint.
-__global__ void jacobi_kernel(int l, double* A, int lda, double* V, int ldv, double* w,
-                              int max_sweeps, double tol, int* sweeps_out) {
-  extern __shared__ double jsh[];
-  const int m = (l + 1) & ~1;
-  const int np = m / 2;
-  double* cs = jsh;            // cos
-  double* sn = jsh + np;       // sin
-  int* P = reinterpret_cast<int*>(jsh + 2 * np);
-  int* Q = P + np;
-  __shared__ double red[32];
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    int i = e % l, j = e / l;
-    V[(size_t)j * ldv + i] = (i == j) ? 1.0 : 0.0;
+// Cyclic two-sided Jacobi for a symmetric l x l matrix in parallel order: a
+// sweep has m - 1 rounds (m = l rounded up to even); in round r the m/2
+// disjoint pairs are (m-1, r) and ((r+i) mod (m-1), (r-i) mod (m-1)),
+// i = 1..m/2-1 (a pair with an index >= l is a padding no-op). One launch per
+// round updates the whole matrix: the rotation of pair i zeroes A[p,q] of the
+// current matrix, and the 2 x 2 block of rows (p_i, q_i) and columns (p_j, q_j)
+// becomes R_i^T A R_j, so every thread transforms its own block(s) reading the
+// previous buffer and writing the next (A is double-buffered; each CTA
+// recomputes the rotations it needs from the previous buffer). V <- V R is
+// updated in place (disjoint column pairs). The off-diagonal mass is checked
+// once per sweep.
+__device__ __forceinline__ void jacobi_pair(int i, int r, int m, int& p, int& q) {
+  if (i == 0) {
+    p = m - 1;
+    q = r;
+  } else {
+    p = (r + i) % (m - 1);
+    q = (r - i + (m - 1)) % (m - 1);
   }
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    // convergence: off-diagonal Frobenius norm vs the diagonal
-    double off = 0.0, dia = 0.0;
-    for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-      int i = e % l, j = e / l;
-      double a = A[(size_t)j * lda + i];
-      if (i == j) dia = fma(a, a, dia);
-      else off = fma(a, a, off);
+  if (p > q) {
+    int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// Rotation (c, s) that zeroes A[p, q] (c = 1, s = 0 for padding or a zero entry).
+__device__ __forceinline__ void jacobi_rot(const double* A, int lda, int l, int p, int q, double& c,
+                                           double& s) {
+  c = 1.0;
+  s = 0.0;
+  if (q >= l) return;
+  const double apq = A[(size_t)q * lda + p];
+  if (apq == 0.0 || fabs(apq) <= 1e-300) return;
+  const double app = A[(size_t)p * lda + p], aqq = A[(size_t)q * lda + q];
+  const double th = (aqq - app) / (2.0 * apq);
+  const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+
+constexpr int kJT = 16;  // pair tile per CTA side
+
+// blockIdx.z = 0: 2 x 2 blocks of A (tile of kJT x kJT pair blocks);
+// blockIdx.z = 1: rows of V (kJT pairs x kJT rows per CTA).
+__global__ void __launch_bounds__(kJT * kJT) jacobi_round_kernel(int l, int m, int r, const double* __restrict__ Ain,
+                                                                 double* __restrict__ Aout, int lda, double* V,
+                                                                 int ldv) {
+  __shared__ double rc[2][kJT], rs[2][kJT];
+  __shared__ int rp[2][kJT], rq[2][kJT];
+  const int np = m / 2;
+  const int tx = threadIdx.x % kJT, ty = threadIdx.x / kJT;
+  if (blockIdx.z == 0) {
+    const int bi0 = blockIdx.y * kJT, bj0 = blockIdx.x * kJT;
+    if (bi0 >= np || bj0 >= np) return;
+    if (threadIdx.x < 2 * kJT) {
+      const int side = threadIdx.x / kJT, t = threadIdx.x % kJT;
+      const int pi = (side == 0 ? bi0 : bj0) + t;
+      int p = 0, q = 0;
+      double c = 1.0, sn = 0.0;
+      if (pi < np) {
+        jacobi_pair(pi, r, m, p, q);
+        jacobi_rot(Ain, lda, l, p, q, c, sn);
+      }
+      rp[side][t] = p; rq[side][t] = q; rc[side][t] = c; rs[side][t] = sn;
     }
     __syncthreads();
-    off = block_sum(off, red);
-    dia = block_sum(dia, red);
-    if (off <= tol * tol * dia || off == 0.0) break;
-    for (int r = 0; r < m - 1; ++r) {
-      for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        int p, q;
-        if (i == 0) { p = m - 1; q = r; }
-        else { p = (r + i) % (m - 1); q = (r - i + (m - 1)) % (m - 1); }
-        if (p > q) { int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        if (q < l) {
-          double apq = A[(size_t)q * lda + p];
-          double app = A[(size_t)p * lda + p], aqq = A[(size_t)q * lda + q];
-          if (apq != 0.0 && fabs(apq) > 1e-300) {
-            double th = (aqq - app) / (2.0 * apq);
-            double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        P[i] = p; Q[i] = q; cs[i] = c; sn[i] = s;
+    const int bi = bi0 + ty, bj = bj0 + tx;
+    if (bi >= np || bj >= np) return;
+    const int p = rp[0][ty], q = rq[0][ty], p2 = rp[1][tx], q2 = rq[1][tx];
+    const double c1 = rc[0][ty], s1 = rs[0][ty], c2 = rc[1][tx], s2 = rs[1][tx];
+    const bool hq = q < l, hq2 = q2 < l;
+    const double a = Ain[(size_t)p2 * lda + p];
+    const double b = hq2 ? Ain[(size_t)q2 * lda + p] : 0.0;
+    const double d = hq ? Ain[(size_t)p2 * lda + q] : 0.0;
+    const double e = (hq && hq2) ? Ain[(size_t)q2 * lda + q] : 0.0;
+    // rows: (p, q) <- (c1 p - s1 q, s1 p + c1 q); then columns likewise with (c2, s2)
+    const double ra = c1 * a - s1 * d, rb = c1 * b - s1 * e;
+    const double rd = s1 * a + c1 * d, re = s1 * b + c1 * e;
+    Aout[(size_t)p2 * lda + p] = c2 * ra - s2 * rb;
+    if (hq2) Aout[(size_t)q2 * lda + p] = s2 * ra + c2 * rb;
+    if (hq) Aout[(size_t)p2 * lda + q] = c2 * rd - s2 * re;
+    if (hq && hq2) Aout[(size_t)q2 * lda + q] = s2 * rd + c2 * re;
+  } else {
+    const int bj0 = blockIdx.x * kJT, row0 = blockIdx.y * kJT;
+    if (bj0 >= np || row0 >= l) return;
+    if (threadIdx.x < kJT) {
+      const int pi = bj0 + threadIdx.x;
+      int p = 0, q = 0;
+      double c = 1.0, sn = 0.0;
+      if (pi < np) {
+        jacobi_pair(pi, r, m, p, q);
+        jacobi_rot(Ain, lda, l, p, q, c, sn);
       }
-      __syncthreads();
-      // rows p, q of A:  A <- J^T A
-      for (int e = threadIdx.x; e < np * l; e += blockDim.x) {
-        int i = e % np, col = e / np;
-        int p = P[i], q = Q[i];
-        if (q >= l || sn[i] == 0.0) continue;
-        double c = cs[i], s = sn[i];
-        double ap = A[(size_t)col * lda + p], aq = A[(size_t)col * lda + q];
-        A[(size_t)col * lda + p] = c * ap - s * aq;
-        A[(size_t)col * lda + q] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns p, q of A and V:  A <- A J, V <- V J
-      for (int e = threadIdx.x; e < np * l; e += blockDim.x) {
-        int i = e % np, row = e / np;
-        int p = P[i], q = Q[i];
-        if (q >= l || sn[i] == 0.0) continue;
-        double c = cs[i], s = sn[i];
-        double ap = A[(size_t)p * lda + row], aq = A[(size_t)q * lda + row];
-        A[(size_t)p * lda + row] = c * ap - s * aq;
-        A[(size_t)q * lda + row] = s * ap + c * aq;
-        double vp = V[(size_t)p * ldv + row], vq = V[(size_t)q * ldv + row];
-        V[(size_t)p * ldv + row] = c * vp - s * vq;
-        V[(size_t)q * ldv + row] = s * vp + c * vq;
-      }
-      __syncthreads();
+      rp[0][threadIdx.x] = p; rq[0][threadIdx.x] = q; rc[0][threadIdx.x] = c; rs[0][threadIdx.x] = sn;
     }
+    __syncthreads();
+    const int pj = bj0 + tx, row = row0 + ty;
+    if (pj >= np || row >= l) return;
+    const int p = rp[0][tx], q = rq[0][tx];
+    const double c = rc[0][tx], sn = rs[0][tx];
+    if (q >= l || sn == 0.0) return;
+    const double vp = V[(size_t)p * ldv + row], vq = V[(size_t)q * ldv + row];
+    V[(size_t)p * ldv + row] = c * vp - sn * vq;
+    V[(size_t)q * ldv + row] = sn * vp + c * vq;
   }
-  for (int i = threadIdx.x; i < l; i += blockDim.x) w[i] = A[(size_t)i * lda + i];
-  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+__global__ void jacobi_init_kernel(int l, const double* A, int lda, double* A0, double* V, int ldv) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)l * l;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % l), j = (int)(e / l);
+    A0[(size_t)j * l + i] = A[(size_t)j * lda + i];
+    V[(size_t)j * ldv + i] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+// out[0] = sum of squared off-diagonal entries, out[1] = sum of squared diagonal entries
+__global__ void jacobi_offnorm_kernel(int l, const double* A, double* out) {
+  __shared__ double red[32];
+  double off = 0.0, dia = 0.0;
+  for (size_t e = threadIdx.x; e < (size_t)l * l; e += blockDim.x) {
+    const int i = (int)(e % l), j = (int)(e / l);
+    const double a = A[e];
+    if (i == j) dia = fma(a, a, dia);
+    else off = fma(a, a, off);
+  }
+  off = block_sum(off, red);
+  __syncthreads();
+  dia = block_sum(dia, red);
+  if (threadIdx.x == 0) {
+    out[0] = off;
+    out[1] = dia;
+  }
+}
+
+__global__ void jacobi_diag_kernel(int l, const double* A, double* w) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < l; i += gridDim.x * blockDim.x)
+    w[i] = A[(size_t)i * l + i];
 }
 
 // Descending order: perm[rank] = i (ties broken by index); w_out, V_out permuted.
@@ -339,12 +397,36 @@ int trtri_lower(int l, const double* L, int ldl, double* X, int ldx, double tiny
   return SC4DVAR_OK;
 }
 
-int jacobi_eig(int l, double* A, int lda, double* V, int ldv, double* w, int max_sweeps, double tol,
-               int* sweeps_dev, cudaStream_t st) {
-  int m = (l + 1) & ~1;
-  size_t smem = (size_t)(m / 2) * (2 * sizeof(double) + 2 * sizeof(int));
-  jacobi_kernel<<<1, 1024, smem, st>>>(l, A, lda, V, ldv, w, max_sweeps, tol, sweeps_dev);
+size_t jacobi_work_bytes(int l) { return ((size_t)2 * l * l + 8) * sizeof(double); }
+
+int jacobi_eig(int l, const double* A, int lda, double* V, int ldv, double* w, int max_sweeps, double tol,
+               void* work, int* sweeps_out, cudaStream_t st) {
+  if (l <= 0) return SC4DVAR_OK;
+  const int m = (l + 1) & ~1, np = m / 2;
+  double* buf[2] = {reinterpret_cast<double*>(work), reinterpret_cast<double*>(work) + (size_t)l * l};
+  double* red = buf[1] + (size_t)l * l;
+  const int nb = (np + kJT - 1) / kJT, nr = (l + kJT - 1) / kJT;
+  const dim3 grid(nb, std::max(nb, nr), 2);
+  jacobi_init_kernel<<<std::min(8 * 152, (int)(((size_t)l * l + 255) / 256)), 256, 0, st>>>(l, A, lda, buf[0],
+                                                                                           V, ldv);
   SC4_LAUNCH_CHECK();
+  int cur = 0, sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    jacobi_offnorm_kernel<<<1, 1024, 0, st>>>(l, buf[cur], red);
+    SC4_LAUNCH_CHECK();
+    double h[2];
+    SC4_CUDA(cudaMemcpyAsync(h, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SC4_CUDA(cudaStreamSynchronize(st));
+    if (h[0] <= tol * tol * h[1] || h[0] == 0.0) break;
+    for (int r = 0; r < m - 1; ++r) {
+      jacobi_round_kernel<<<grid, kJT * kJT, 0, st>>>(l, m, r, buf[cur], buf[cur ^ 1], l, V, ldv);
+      SC4_LAUNCH_CHECK();
+      cur ^= 1;
+    }
+  }
+  jacobi_diag_kernel<<<(l + 255) / 256, 256, 0, st>>>(l, buf[cur], w);
+  SC4_LAUNCH_CHECK();
+  if (sweeps_out) *sweeps_out = sweep;
   return SC4DVAR_OK;
 }
 

@@ -11,8 +11,12 @@ int gemm_nn(int rows, int kk, int c, double alpha, const TA* A, int lda, const d
             int transB, double beta, TC* C, int ldc, cudaStream_t st);
 int chol_lower(int l, double* A, int lda, int* info_dev, cudaStream_t st);
 int trtri_lower(int l, const double* L, int ldl, double* X, int ldx, double tiny, cudaStream_t st);
-int jacobi_eig(int l, double* A, int lda, double* V, int ldv, double* w, int max_sweeps, double tol,
-               int* sweeps_dev, cudaStream_t st);
+// Symmetric eigen-decomposition (FP64 Jacobi): A (l x l, not modified) = V diag(w) V^T,
+// eigenvalues unsorted. work: jacobi_work_bytes(l) of device memory. Synchronizes
+// the stream once per sweep (convergence test); sweeps_out (host, nullable).
+size_t jacobi_work_bytes(int l);
+int jacobi_eig(int l, const double* A, int lda, double* V, int ldv, double* w, int max_sweeps, double tol,
+               void* work, int* sweeps_out, cudaStream_t st);
 int sort_desc(int l, const double* w, const double* V, int ldv, double* w_out, double* V_out,
               int ldo, cudaStream_t st);
 int power_lmax(int l, const double* G, int ldg, double* out_dev, cudaStream_t st);

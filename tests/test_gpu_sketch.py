@@ -24,11 +24,13 @@ def hhat_action(V, lam, X):
     return V @ (lam[:, None] * (V.T @ X))
 
 
-@pytest.mark.parametrize("method", ["randsvd", "nystrom", "singleview"])
-def test_sketch_matches_oracle_given_omega(small, method):
+@pytest.mark.parametrize("method,l", [("randsvd", 20), ("nystrom", 20), ("singleview", 20),
+                                      ("randsvd", 21), ("nystrom", 33)])
+def test_sketch_matches_oracle_given_omega(small, method, l):
+    """l = 20 is the workload's size; odd l exercises the padding pair of the
+    parallel-order Jacobi eigen-solver of the thin SVD."""
     from oracle import philox, sketch
     wl, prob, ref = small
-    l = wl.k
     Om = philox.gaussian(wl.seed, 100, wl.n, l)
     Ps = philox.gaussian(wl.seed, 1100, wl.m, 2 * l + 1)
     pc = prob.build_precond(method, l=l, Omega=torch.tensor(Om.T.copy(), device="cuda"),
