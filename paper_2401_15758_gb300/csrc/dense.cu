@@ -4,8 +4,14 @@
 //             (tall-skinny Gram products: Y^T Y, Omega^T Y, Psi^T Q, Q^T Y).
 // * gemm_nn:  C (rows x c) = alpha A B + beta C, A rows x kk, B kk x c (or B^T)
 //             (Q = Y L^{-T}, V = W^T U Sigma^{-1}, reorthogonalisation updates).
-// Both accumulate in FP64 whatever the storage type of A / B (FP32 products are
-// exact in FP64, so the Gram matrices of CholeskyQR2 keep FP64 accuracy).
+// FP64 operands accumulate in FP64. FP32 operands avoid the FP64 pipe, which
+// runs at 1/64 of the FP32 rate on this GPU: gemm_tn keeps every product exactly
+// as a float pair (rounded product + FMA residual) and sums pairs with TwoSum
+// into a (hi, lo) float accumulator, so its Gram matrices keep FP64-level
+// accuracy (relative error ~1e-14) for CholeskyQR2; gemm_nn (products with a
+// small factor: Y L^{-T}, W^T U Sigma^{-1}, projections) accumulates in FP32,
+// the precision of its FP32 output. Symmetric Gram products (A == B) compute
+// the upper tiles only and mirror them.
 // * Small l x l factorizations on one CTA: Cholesky (lower), triangular inverse,
 //   cyclic Jacobi eigensolver in round-robin (circle) order, descending sort.
 // * Vector helpers for PCG with deterministic two-pass reductions.
@@ -77,6 +83,165 @@ int gemm_tn(int rows, int la, int lb, double alpha, const TA* A, int lda, const 
   return SC4DVAR_OK;
 }
 
+// ---- FP32 operands: double-float accumulation (gemm_tn) ----
+// (s, c) += a * b with the exact product p + e (p = fl(a b), e = fma(a, b, -p))
+// and TwoSum of s and p (Knuth); the explicit _rn intrinsics keep the compiler
+// from fusing the product into the sum.
+__device__ __forceinline__ void dfloat_acc(float a, float b, float& s, float& c) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float bv = __fsub_rn(t, s);
+  const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(er, e));
+}
+
+constexpr int kGT = 64;   // output tile (kGT x kGT) of the FP32 Gram kernel
+constexpr int kGR = 32;   // rows per shared-memory stage
+
+// C (la x lb) += alpha A^T B over one chunk of rows (grid.z); 256 threads, 4 x 4
+// outputs each; sym: A == B, tiles below the diagonal skipped.
+__global__ void __launch_bounds__(256) gemm_tn_f32_kernel(int rows, int la, int lb, int rows_per_chunk,
+                                                          double alpha, const float* __restrict__ A, int lda,
+                                                          const float* __restrict__ B, int ldb, double* C,
+                                                          int ldc, int sym) {
+  __shared__ __align__(16) float As[kGR][kGT];
+  __shared__ __align__(16) float Bs[kGR][kGT];
+  const int i0 = blockIdx.x * kGT, j0 = blockIdx.y * kGT;
+  if (sym && j0 + kGT <= i0) return;
+  const int r_begin = blockIdx.z * rows_per_chunk;
+  const int r_end = min(rows, r_begin + rows_per_chunk);
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
+  for (int r0 = r_begin; r0 < r_end; r0 += kGR) {
+    for (int e = threadIdx.x; e < kGR * kGT; e += 256) {
+      const int rr = e % kGR, cc = e / kGR;
+      const int r = r0 + rr;
+      As[rr][cc] = (r < r_end && i0 + cc < la) ? A[(size_t)(i0 + cc) * lda + r] : 0.f;
+      Bs[rr][cc] = (r < r_end && j0 + cc < lb) ? B[(size_t)(j0 + cc) * ldb + r] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < kGR; ++rr) {
+      const float4 av = *reinterpret_cast<const float4*>(&As[rr][ti * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[rr][tj * 4]);
+      const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dfloat_acc(a4[a], b4[b], sh[a][b], sl[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ti * 4 + a, j = j0 + tj * 4 + b;
+      if (i < la && j < lb && (!sym || j >= i))
+        atomicAdd(&C[(size_t)j * ldc + i], alpha * ((double)sh[a][b] + (double)sl[a][b]));
+    }
+}
+
+// lower triangle <- upper triangle
+__global__ void mirror_upper_kernel(int l, double* C, int ldc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < l * l) {
+    const int i = idx % l, j = idx / l;
+    if (i > j) C[(size_t)j * ldc + i] = C[(size_t)i * ldc + j];
+  }
+}
+
+template <>
+int gemm_tn<float, float>(int rows, int la, int lb, double alpha, const float* A, int lda, const float* B,
+                          int ldb, double beta, double* C, int ldc, cudaStream_t st) {
+  if (la <= 0 || lb <= 0) return SC4DVAR_OK;
+  scale_matrix_kernel<<<div_up(la * lb, 256), 256, 0, st>>>(la, lb, beta, C, ldc);
+  SC4_LAUNCH_CHECK();
+  if (rows <= 0) return SC4DVAR_OK;
+  const int sym = (A == B && la == lb && lda == ldb && beta == 0.0) ? 1 : 0;
+  const int ta = div_up(la, kGT), tb = div_up(lb, kGT);
+  const int tiles = sym ? ta * (ta + 1) / 2 : ta * tb;
+  int chunks = max(1, min(div_up(rows, 256), div_up(4 * 152, tiles)));
+  int rpc = div_up(div_up(rows, chunks), kGR) * kGR;
+  chunks = div_up(rows, rpc);
+  gemm_tn_f32_kernel<<<dim3(ta, tb, chunks), 256, 0, st>>>(rows, la, lb, rpc, alpha, A, lda, B, ldb, C, ldc,
+                                                           sym);
+  SC4_LAUNCH_CHECK();
+  if (sym) {
+    mirror_upper_kernel<<<div_up(la * la, 256), 256, 0, st>>>(la, C, ldc);
+    SC4_LAUNCH_CHECK();
+  }
+  return SC4DVAR_OK;
+}
+
+// ---- FP32 operands: FP32 accumulation (gemm_nn) ----
+// C (rows x c) = alpha A op(B) + beta C; tile 128 rows x 64 columns per CTA,
+// 256 threads with 8 x 4 outputs each, k in stages of 32.
+template <typename TC>
+__global__ void __launch_bounds__(256) gemm_nn_f32_kernel(int rows, int kk, int c, float alpha,
+                                                          const float* __restrict__ A, int lda,
+                                                          const double* __restrict__ B, int ldb, int transB,
+                                                          double beta, TC* __restrict__ C, int ldc) {
+  __shared__ __align__(16) float As[32][128];  // [k][row]
+  __shared__ __align__(16) float Bs[32][64];   // [k][col]
+  const int r0 = blockIdx.x * 128, c0 = blockIdx.y * 64;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;  // 16 row groups of 8, 16 column groups of 4
+  float acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int k0 = 0; k0 < kk; k0 += 32) {
+    for (int e = threadIdx.x; e < 32 * 128; e += 256) {
+      const int rr = e & 127, kc = e >> 7;
+      const int r = r0 + rr, k = k0 + kc;
+      As[kc][rr] = (r < rows && k < kk) ? A[(size_t)k * lda + r] : 0.f;
+    }
+    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+      const int kc = e & 31, cc = e >> 5;
+      const int k = k0 + kc, j = c0 + cc;
+      float v = 0.f;
+      if (k < kk && j < c) v = (float)(transB ? B[(size_t)k * ldb + j] : B[(size_t)j * ldb + k]);
+      Bs[kc][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kc = 0; kc < 32; ++kc) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kc][tr * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kc][tr * 8 + 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[kc][tc * 4]);
+      const float a8[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(a8[a], b4[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int j = c0 + tc * 4 + b;
+    if (j >= c) continue;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int r = r0 + tr * 8 + a;
+      if (r < rows) {
+        TC* p = &C[(size_t)j * ldc + r];
+        double v = (double)(alpha * acc[a][b]);
+        if (beta != 0.0) v += beta * (double)*p;
+        *p = (TC)v;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ gemm_nn
 // C = alpha * A * op(B) + beta * C; op(B) = B (kk x c) or B^T (B stored c x kk).
 template <typename TA, typename TC>
@@ -131,6 +296,14 @@ template <typename TA, typename TC>
 int gemm_nn(int rows, int kk, int c, double alpha, const TA* A, int lda, const double* B, int ldb,
             int transB, double beta, TC* C, int ldc, cudaStream_t st) {
   if (rows <= 0 || c <= 0) return SC4DVAR_OK;
+  if constexpr (sizeof(TA) == 4) {
+    if (c > 1) {  // single-vector products keep FP64 accumulation (Remark 1 applies inside PCG)
+      gemm_nn_f32_kernel<TC><<<dim3(div_up(rows, 128), div_up(c, 64)), 256, 0, st>>>(
+          rows, kk, c, (float)alpha, A, lda, B, ldb, transB, beta, C, ldc);
+      SC4_LAUNCH_CHECK();
+      return SC4DVAR_OK;
+    }
+  }
   dim3 grid(div_up(rows, 64), div_up(c, 32));
   gemm_nn_kernel<TA, TC><<<grid, 256, 0, st>>>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C,
                                               ldc);
@@ -557,8 +730,6 @@ int woodbury_apply(int n, int l, int k, const double* V, int ldv, const double* 
 // ---- explicit instantiations ---------------------------------------------------
 template int gemm_tn<double, double>(int, int, int, double, const double*, int, const double*, int,
                                      double, double*, int, cudaStream_t);
-template int gemm_tn<float, float>(int, int, int, double, const float*, int, const float*, int,
-                                   double, double*, int, cudaStream_t);
 template int gemm_tn<double, float>(int, int, int, double, const double*, int, const float*, int,
                                     double, double*, int, cudaStream_t);
 template int gemm_tn<float, double>(int, int, int, double, const float*, int, const double*, int,

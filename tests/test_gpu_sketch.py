@@ -57,6 +57,33 @@ def test_sketch_matches_oracle_given_omega(small, method, l):
     assert rel(back, R.T) <= 1e-10
 
 
+@pytest.mark.parametrize("method,l", [("randsvd", 20), ("nystrom", 20), ("singleview", 20),
+                                      ("randsvd", 21)])
+def test_fp32_sketch_close_to_oracle(small, method, l):
+    """FP32 sketches (FP32 sweeps, double-float Gram products, FP32 tall
+    products) against the FP64 oracle given the same Omega / Psi: the action of
+    H_hat to FP32 accuracy, V orthonormal to FP32 accuracy. The Nystrom shift
+    uses the unit roundoff of the precision that forms Y (2^-24 here) on both
+    sides."""
+    import paper_2401_15758_gb300 as g
+    from oracle import philox, sketch
+    wl, prob, ref = small
+    Om = philox.gaussian(wl.seed, 100, wl.n, l)
+    Ps = philox.gaussian(wl.seed, 1100, wl.m, 2 * l + 1)
+    pc = prob.build_precond(method, l=l, prec=g.FP32, Omega=torch.tensor(Om.T.copy(), device="cuda"),
+                            Psi=torch.tensor(Ps.T.copy(), device="cuda"))
+    V, lam = pc.arrays()
+    if method == "randsvd":
+        lr = sketch.randsvd(ref.A, ref.At, Om)
+    elif method == "nystrom":
+        lr = sketch.nystrom(ref.misfit_hvp, Om, eps=2.0 ** -24)
+    else:
+        lr = sketch.singleview(ref.A, ref.At, Om, Ps)
+    X = np.random.default_rng(1).standard_normal((wl.n, 4))
+    assert rel(hhat_action(V, lam, X), hhat_action(lr.V, lr.lam, X)) <= 1e-4
+    assert np.max(np.abs(V.T @ V - np.eye(V.shape[1]))) <= 1e-5
+
+
 def test_philox_drawn_sketch_equals_given_omega(small):
     from oracle import philox
     wl, prob, ref = small
