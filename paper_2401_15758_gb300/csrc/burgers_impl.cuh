@@ -408,7 +408,9 @@ static int pick_cluster(int n, int k, size_t tb, int kind) {
          cl < 16)
     cl *= 2;
   if (k <= 4) {
-    while (cl < 8 && n / (cl * 2) >= 512) cl *= 2;
+    // few directions: spread each over up to 16 CTAs (non-portable cluster size)
+    // while a CTA keeps at least 512 points
+    while (cl < 16 && n / (cl * 2) >= 512) cl *= 2;
   }
   return cl;
 }

@@ -145,7 +145,7 @@ V2_CASES = [
     (8192, 20, 6, "fp32"),   # packed FP32x2, 8 pairs per thread, one CTA per direction
     (8192, 20, 3, "fp32"),   # packed FP32x2 in an 8-CTA cluster (few directions)
     (512, 20, 5, "fp32"),    # scalar register-resident kernels
-    (8192, 20, 2, "fp64"),   # 8-CTA cluster, 1024 points per CTA (few directions)
+    (8192, 20, 2, "fp64"),   # 16-CTA cluster, 512 points per CTA (few directions)
     (2048, 20, 5, "fp64"),   # 2 points per thread, odd k (FFT pair tail)
     (1024, 20, 1, "fp32"),   # 2-CTA cluster
 ]
