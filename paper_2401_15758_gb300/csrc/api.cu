@@ -205,8 +205,8 @@ static int hvp_block(Prob* P, const T* X, int ldx, int k, T* Y, int ldy, int mis
   return SC4DVAR_OK;
 }
 
-// q = (I + H) p for one FP64 vector, operator arithmetic in prec.
-static int hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t st) {
+// q = (I + H) p for one FP64 vector, operator arithmetic in prec (launches only).
+static int hvp_vec_launch(Prob* P, const double* p, double* q, int prec, cudaStream_t st) {
   if (prec == SC4DVAR_FP64) return hvp_block<double>(P, p, P->n, 1, q, P->n, 0, st);
   int n = P->n, m = P->m;
   SC4_TRY(P->wU.ensure((size_t)n * sizeof(float)));
@@ -219,6 +219,76 @@ static int hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t s
   SC4_TRY(model_tlm<float>(P, U, n, 1, W, m, st));
   SC4_TRY(model_adj<float>(P, W, m, 1, L, n, st));
   SC4_TRY(prior_any<float, double, double>(P, 1, L, n, q, n, p, n, st));
+  count(P, 1, 1);
+  return SC4DVAR_OK;
+}
+
+// Vorticity problems run a single-vector product as thousands of small
+// launches (every RK stage of both sweeps is a 2D transform and a stencil
+// kernel), so it is recorded once per (p, q, precision) as a CUDA graph on the
+// handle's private stream and replayed on the caller's stream. The first call
+// of a key runs eagerly (it sizes the work arrays, so nothing allocates during
+// recording); a recording is discarded when a work array has moved since.
+static void hvp_bufs(Prob* P, void* (&b)[5]) {
+  b[0] = P->wBve.p; b[1] = P->wCplx.p; b[2] = P->wU.p; b[3] = P->wW.p; b[4] = P->wL.p;
+}
+
+static int hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t st) {
+  if (!is_bve(P)) return hvp_vec_launch(P, p, q, prec, st);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return hvp_vec_launch(P, p, q, prec, st);
+  }
+  Prob::HvpGraph* e = nullptr;
+  for (auto& g : P->hvp_graphs)
+    if (g.p == p && g.q == q && g.prec == prec) e = &g;
+  if (!e) {
+    SC4_TRY(hvp_vec_launch(P, p, q, prec, st));
+    if (P->hvp_graphs.size() >= 8) {
+      if (P->hvp_graphs.front().exec) cudaGraphExecDestroy(P->hvp_graphs.front().exec);
+      P->hvp_graphs.erase(P->hvp_graphs.begin());
+    }
+    Prob::HvpGraph g{p, q, prec, {}, nullptr, false};
+    hvp_bufs(P, g.bufs);
+    P->hvp_graphs.push_back(g);
+    return SC4DVAR_OK;
+  }
+  void* now[5];
+  hvp_bufs(P, now);
+  bool same = true;
+  for (int i = 0; i < 5; ++i) same = same && now[i] == e->bufs[i];
+  if (e->exec && !same) {
+    cudaGraphExecDestroy(e->exec);
+    e->exec = nullptr;
+  }
+  if (!e->exec && !e->eager_only) {
+    if (!P->graph_stream) SC4_CUDA(cudaStreamCreateWithFlags(&P->graph_stream, cudaStreamNonBlocking));
+    SC4_CUDA(cudaStreamSynchronize(st));
+    const sc4dvar_counters_t saved = P->counters;
+    cudaGraph_t graph = nullptr;
+    int rc = SC4DVAR_OK;
+    if (cudaStreamBeginCapture(P->graph_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = SC4DVAR_ERR_CUDA;
+    } else {
+      rc = hvp_vec_launch(P, p, q, prec, P->graph_stream);
+      if (cudaStreamEndCapture(P->graph_stream, &graph) != cudaSuccess) rc = SC4DVAR_ERR_CUDA;
+    }
+    P->counters = saved;  // recording executes nothing
+    if (rc == SC4DVAR_OK && graph && cudaGraphInstantiate(&e->exec, graph, 0) != cudaSuccess) {
+      e->exec = nullptr;
+      rc = SC4DVAR_ERR_CUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != SC4DVAR_OK) {
+      cudaGetLastError();
+      e->eager_only = true;  // the same kernels, launched one by one
+    } else {
+      hvp_bufs(P, e->bufs);
+    }
+  }
+  if (!e->exec) return hvp_vec_launch(P, p, q, prec, st);
+  SC4_CUDA(cudaGraphLaunch(e->exec, st));
   count(P, 1, 1);
   return SC4DVAR_OK;
 }
@@ -1078,6 +1148,9 @@ int sc4dvar_problem_destroy(sc4dvar_problem_t P) {
   cudaFree(P->bve_tabc64); cudaFree(P->bve_tabc32);
   cudaFree(P->bve_q64); cudaFree(P->bve_p64); cudaFree(P->bve_q32); cudaFree(P->bve_p32);
   cudaFree(P->bve_ckpt); cudaFree(P->bve_rws);
+  for (auto& g : P->hvp_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
   P->wBve.release(); P->wCplx.release();
   P->wU.release(); P->wW.release(); P->wL.release(); P->part.release(); P->scal.release();
   P->vec.release();

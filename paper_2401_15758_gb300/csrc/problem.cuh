@@ -68,6 +68,18 @@ struct sc4dvar_problem_s {
   sc4::Buf wU, wW, wL, part, scal, vec;
   int count_mode = sc4::kOnline;
   sc4dvar_counters_t counters{};
+  // single-vector Hessian products recorded as CUDA graphs (vorticity problems):
+  // key (p, q, precision) plus the work-array addresses the recording used
+  struct HvpGraph {
+    const double* p;
+    double* q;
+    int prec;
+    void* bufs[5];
+    cudaGraphExec_t exec;
+    bool eager_only;
+  };
+  std::vector<HvpGraph> hvp_graphs;
+  cudaStream_t graph_stream = nullptr;
 };
 
 struct sc4dvar_precond_s {
