@@ -249,7 +249,7 @@ template <typename C, typename RI, int R>
 __global__ void __launch_bounds__(256) wfft_rows_fwd(int N, int k, const RI* __restrict__ X, int ldx,
                                                      C* cbuf, const C* __restrict__ tw) {
   using Rl = typename CplxOf<C>::R;
-  const int lane = threadIdx.x & 31, j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int p = blockIdx.y, fa = 2 * p, fb = 2 * p + 1;
   if (j >= N) return;
   const bool hasb = fb < k;
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(256) wfft_rows_inv(int N, int k, const C* cbuf
                                                      int ldy, const RZ* __restrict__ Z, int ldz,
                                                      const C* __restrict__ tw) {
   using Rl = typename CplxOf<C>::R;
-  const int lane = threadIdx.x & 31, j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int p = blockIdx.y, fa = 2 * p, fb = 2 * p + 1;
   if (j >= N) return;
   const bool hasb = fb < k;
@@ -809,17 +809,29 @@ static void launch_cols(int pairs, C* cb, const typename CplxOf<C>::R* tab, cons
   kc<<<dim3(N / CB, pairs), G * CB, smc, st>>>(cb, tab, tw);
 }
 
+// Rows per block of the row transforms (one warp per row): 8, fewer when the
+// grid would not cover the GPU twice (single fields).
+static int rows_per_block(int N, int pairs) {
+  int rpb = 8;
+  while (rpb > 1 && (N / rpb) * pairs < 2 * 152) rpb /= 2;
+  return rpb;
+}
+
 template <typename C, typename RI, typename RO, typename RZ, int RR>
 static int wfft2(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, const RZ* Z, int ldz,
                  const double* table, C* cb, cudaStream_t st) {
   constexpr int N = RR * 32;
   const int pairs = (k + 1) / 2;
-  wfft_rows_fwd<C, RI, RR><<<dim3(div_up(N, 8), pairs), 256, 0, st>>>(N, k, X, ldx, cb, tw_of<C>(g));
+  const int rpb = rows_per_block(N, pairs);
+  wfft_rows_fwd<C, RI, RR><<<dim3(N / rpb, pairs), 32 * rpb, 0, st>>>(N, k, X, ldx, cb, tw_of<C>(g));
   SC4_LAUNCH_CHECK();
   using Rl = typename CplxOf<C>::R;
   const Rl* tab = reinterpret_cast<const Rl*>(table_brev(g, table, sizeof(Rl)));
   int rc = SC4DVAR_OK;
-  if constexpr (sizeof(C) == 8 && N >= 256) {
+  if (N >= 128 && pairs * (N / 8) < 2 * 152) {
+    // single fields: two columns per block spread the transform over the GPU
+    launch_cols<C, N, 2, 0>(pairs, cb, tab, tw_of<C>(g), st, &rc);
+  } else if constexpr (sizeof(C) == 8 && N >= 256) {
     switch (cols_shape(N)) {
       case 0: launch_cols<C, N, 16, 0>(pairs, cb, tab, tw_of<C>(g), st, &rc); break;
       case 1: launch_cols<C, N, 16, 64>(pairs, cb, tab, tw_of<C>(g), st, &rc); break;
@@ -834,7 +846,7 @@ static int wfft2(const BveGeom& g, int k, const RI* X, int ldx, RO* Y, int ldy, 
     return rc;
   }
   SC4_LAUNCH_CHECK();
-  wfft_rows_inv<C, RO, RZ, RR><<<dim3(div_up(N, 8), pairs), 256, 0, st>>>(N, k, cb, Y, ldy, Z, ldz,
+  wfft_rows_inv<C, RO, RZ, RR><<<dim3(N / rpb, pairs), 32 * rpb, 0, st>>>(N, k, cb, Y, ldy, Z, ldz,
                                                                           tw_of<C>(g));
   SC4_LAUNCH_CHECK();
   return SC4DVAR_OK;
@@ -910,13 +922,14 @@ static StencilConsts consts(const BveGeom& g) {
 }
 
 // Launch grid of the tiled stencil kernels for k fields, and the dispatch on
-// the tile width TX = min(N, 64).
+// the tile width: TX = min(N, 64), or 32 for one or two fields (four times the
+// blocks of a single field, so it spreads over the GPU).
 template <typename T, int TX>
 static dim3 sgrid(int N, int k) { return dim3(N / TX, N / TileGeom<T, TX>::TY, k); }
 #define SC4_STENCIL(N, KERNEL, T, ...)                                                          \
   do {                                                                                          \
-    if ((N) >= 64) KERNEL<T, 64><<<sgrid<T, 64>(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);    \
-    else if ((N) == 32) KERNEL<T, 32><<<sgrid<T, 32>(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__); \
+    if ((N) >= 64 && kz > 2) KERNEL<T, 64><<<sgrid<T, 64>(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__); \
+    else if ((N) >= 32) KERNEL<T, 32><<<sgrid<T, 32>(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__); \
     else KERNEL<T, 16><<<sgrid<T, 16>(N, kz), kTileThreads, 0, st>>>(__VA_ARGS__);              \
     SC4_LAUNCH_CHECK();                                                                         \
   } while (0)
