@@ -718,6 +718,174 @@ __global__ void __launch_bounds__(kTileThreads) bve_adj_stage_kernel(int N, Sten
   }
 }
 
+// ---- two directions per thread in packed FP32x2 (FP32 blocks, N >= 64) ----
+// Thread (tx, band) of block (x, y, zp) computes directions z = 2 zp and
+// 2 zp + 1 at the same points: their values travel as float2 pairs (one
+// 4-byte shared load per direction, no reshuffling), the base stencils (q_s,
+// psi_s) are read once and broadcast to both lanes, and the stencil arithmetic
+// runs on packed FP32x2 instructions. For odd k the last pair repeats
+// direction z in its second lane and does not store it. Used for the TLM stage
+// and the ADJ Jacobian (the ADJ stage kernel measured faster in scalar form,
+// at higher occupancy).
+using pf2 = float2;
+__device__ __forceinline__ pf2 pmk(float a) { return make_float2(a, a); }
+__device__ __forceinline__ pf2 padd(pf2 a, pf2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ pf2 pmul(pf2 a, pf2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ pf2 pfma(pf2 a, pf2 b, pf2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ pf2 psub(pf2 a, pf2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+struct St9p {
+  pf2 c, e, w, n, s, ne, nw, se, sw;
+};
+
+__device__ __forceinline__ St9p bcast9(const St9<float>& v) {
+  St9p o;
+  o.c = pmk(v.c); o.e = pmk(v.e); o.w = pmk(v.w); o.n = pmk(v.n); o.s = pmk(v.s);
+  o.ne = pmk(v.ne); o.nw = pmk(v.nw); o.se = pmk(v.se); o.sw = pmk(v.sw);
+  return o;
+}
+
+// 12 d^2 J_A(a, b) on packed pairs (the three Jacobians of arakawa12)
+__device__ __forceinline__ pf2 arakawa12p(const St9p& a, const St9p& b) {
+  pf2 jpp = pfma(psub(a.e, a.w), psub(b.n, b.s), pmul(psub(a.s, a.n), psub(b.e, b.w)));
+  pf2 jpx = pfma(a.e, psub(b.ne, b.se),
+                 pfma(a.w, psub(b.sw, b.nw), pfma(a.n, psub(b.nw, b.ne), pmul(a.s, psub(b.se, b.sw)))));
+  pf2 jxp = pfma(b.n, psub(a.ne, a.nw),
+                 pfma(b.s, psub(a.sw, a.se), pfma(b.e, psub(a.se, a.ne), pmul(b.w, psub(a.nw, a.sw)))));
+  return padd(padd(jpp, jpx), jxp);
+}
+
+__device__ __forceinline__ pf2 lap5p(const St9p& a) {
+  return pfma(a.c, pmk(-4.f), padd(padd(a.e, a.w), padd(a.n, a.s)));
+}
+
+// three-row window over the same column of two staged tiles (two directions)
+struct TileWin2 {
+  const float* a;
+  const float* b;
+  pf2 sw, sc, se, mw, mc, me, nw, nc, ne;
+  __device__ __forceinline__ void ld(int trow, pf2& w, pf2& c, pf2& e) const {
+    const float* pa = a + trow * TileGeom<float, 64>::W;
+    const float* pb = b + trow * TileGeom<float, 64>::W;
+    w = make_float2(pa[-1], pb[-1]);
+    c = make_float2(pa[0], pb[0]);
+    e = make_float2(pa[1], pb[1]);
+  }
+  __device__ __forceinline__ void init(const float* ta, const float* tb, int tx, int ty) {
+    a = ta + TileGeom<float, 64>::O + tx;
+    b = tb + TileGeom<float, 64>::O + tx;
+    ld(ty, sw, sc, se);
+    ld(ty + 1, mw, mc, me);
+    ld(ty + 2, nw, nc, ne);
+  }
+  __device__ __forceinline__ void advance(int ty) {
+    sw = mw; sc = mc; se = me;
+    mw = nw; mc = nc; me = ne;
+    ld(ty + 2, nw, nc, ne);
+  }
+  __device__ __forceinline__ St9p st() const {
+    St9p v;
+    v.c = mc; v.e = me; v.w = mw;
+    v.n = nc; v.s = sc; v.ne = ne; v.nw = nw; v.se = se; v.sw = sw;
+    return v;
+  }
+};
+
+__device__ __forceinline__ pf2 ld2(const float* f, size_t o0, size_t o1) { return make_float2(f[o0], f[o1]); }
+__device__ __forceinline__ void st2(float* f, size_t o0, size_t o1, bool has1, pf2 v) {
+  f[o0] = v.x;
+  if (has1) f[o1] = v.y;
+}
+
+constexpr int kD2TlmTiles = 6;
+
+__global__ void __launch_bounds__(kTileThreads) bve_tlm_stage_d2_kernel(int N, StencilConsts sc, int s, float h,
+                                                                        const float* __restrict__ qb,
+                                                                        const float* __restrict__ pb,
+                                                                        const float* __restrict__ cur,
+                                                                        const float* __restrict__ dpsi,
+                                                                        float* acc, float* dx, float* next,
+                                                                        size_t ld, int k) {
+  using TG = TileGeom<float, 64>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* sq = reinterpret_cast<float*>(smraw);
+  float* sp = sq + TG::SIZE;
+  float* sd0 = sp + TG::SIZE;
+  float* sd1 = sd0 + TG::SIZE;
+  float* sg0 = sd1 + TG::SIZE;
+  float* sg1 = sg0 + TG::SIZE;
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * TG::TY;
+  const int tx = threadIdx.x % 64, ty0 = (threadIdx.x / 64) * TG::P;
+  const int z0 = 2 * blockIdx.z;
+  const bool has1 = z0 + 1 < k;
+  const size_t off0 = (size_t)z0 * ld, off1 = has1 ? off0 + ld : off0;
+  pf2 a_r[TG::P], x_r[TG::P];
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    const size_t g = (size_t)(j0 + ty0 + r) * N + i0 + tx;
+    a_r[r] = s == 0 ? pmk(0.f) : ld2(acc, off0 + g, off1 + g);
+    x_r[r] = ld2(dx, off0 + g, off1 + g);
+  }
+  tile_load<float, 64>(sd0, cur + off0, N, i0, j0);
+  tile_load<float, 64>(sd1, cur + off1, N, i0, j0);
+  tile_load<float, 64>(sg0, dpsi + off0, N, i0, j0);
+  tile_load<float, 64>(sg1, dpsi + off1, N, i0, j0);
+  tile_load<float, 64>(sq, qb, N, i0, j0);
+  tile_load<float, 64>(sp, pb, N, i0, j0);
+  tile_wait();
+  const pf2 bs = pmk((float)kBveB[s]);
+  const pf2 ha = pmk((s < 3) ? h * (float)kBveA[s] : 0.f);
+  const pf2 mc12 = pmk(-(float)sc.c12), nudd = pmk((float)sc.nudd), h2 = pmk(h);
+  TileWin<float, 64> q, ps;
+  TileWin2 d, dp;
+  q.init(sq, tx, ty0);
+  ps.init(sp, tx, ty0);
+  d.init(sd0, sd1, tx, ty0);
+  dp.init(sg0, sg1, tx, ty0);
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    if (r) { q.advance(ty0 + r); ps.advance(ty0 + r); d.advance(ty0 + r); dp.advance(ty0 + r); }
+    const St9p qq = bcast9(q.st()), pp = bcast9(ps.st()), dd = d.st(), ddp = dp.st();
+    const pf2 dk = pfma(mc12, padd(arakawa12p(ddp, qq), arakawa12p(pp, dd)), pmul(nudd, lap5p(dd)));
+    const size_t g = (size_t)(j0 + ty0 + r) * N + i0 + tx;
+    const pf2 a = pfma(bs, dk, a_r[r]);
+    if (s < 3) {
+      st2(acc, off0 + g, off1 + g, has1, a);
+      st2(next, off0 + g, off1 + g, has1, pfma(ha, dk, x_r[r]));
+    } else {
+      st2(dx, off0 + g, off1 + g, has1, pfma(h2, a, x_r[r]));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTileThreads) bve_adj_jac_d2_kernel(int N, StencilConsts sc,
+                                                                      const float* __restrict__ qb,
+                                                                      const float* __restrict__ kap, float* t1,
+                                                                      size_t ld, int k) {
+  using TG = TileGeom<float, 64>;
+  __shared__ __align__(16) float sq[TG::SIZE], sk0[TG::SIZE], sk1[TG::SIZE];
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * TG::TY;
+  const int tx = threadIdx.x % 64, ty0 = (threadIdx.x / 64) * TG::P;
+  const int z0 = 2 * blockIdx.z;
+  const bool has1 = z0 + 1 < k;
+  const size_t off0 = (size_t)z0 * ld, off1 = has1 ? off0 + ld : off0;
+  tile_load<float, 64>(sk0, kap + off0, N, i0, j0);
+  tile_load<float, 64>(sk1, kap + off1, N, i0, j0);
+  tile_load<float, 64>(sq, qb, N, i0, j0);
+  tile_wait();
+  const pf2 c12 = pmk((float)sc.c12);
+  TileWin<float, 64> q;
+  TileWin2 kk;
+  q.init(sq, tx, ty0);
+  kk.init(sk0, sk1, tx, ty0);
+#pragma unroll
+  for (int r = 0; r < TG::P; ++r) {
+    if (r) { q.advance(ty0 + r); kk.advance(ty0 + r); }
+    const size_t g = (size_t)(j0 + ty0 + r) * N + i0 + tx;
+    st2(t1, off0 + g, off1 + g, has1, pmul(c12, arakawa12p(bcast9(q.st()), kk.st())));
+  }
+}
+
 template <typename T>
 __global__ void scale_fields_kernel(size_t total, T a, const T* __restrict__ x, T* y) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -1104,8 +1272,18 @@ int bve_tlm(const BveGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* 
         size_t row = (size_t)(4 * (t - base) + s) * n;
         SC4_TRY(fft2_apply<T, T, T, T>(g, k, cur, (int)n, dpsi, (int)n, (const T*)nullptr, 0, g.poisson,
                                        cbuf, st));
-        SC4_STENCIL(N, bve_tlm_stage_kernel, T, N, sc, s, (T)g.h, qbase<T>(g) + row, pbase<T>(g) + row,
-                    cur, dpsi, acc, dx, nxt, n);
+        if (sizeof(T) == 4 && N >= 64 && k > 2) {
+          const size_t smd = (size_t)kD2TlmTiles * TileGeom<float, 64>::SIZE * sizeof(float);
+          SC4_CUDA(cudaFuncSetAttribute(bve_tlm_stage_d2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smd));
+          bve_tlm_stage_d2_kernel<<<sgrid<float, 64>(N, (k + 1) / 2), kTileThreads, smd, st>>>(
+              N, sc, s, (float)g.h, (const float*)(qbase<T>(g) + row), (const float*)(pbase<T>(g) + row),
+              (const float*)cur, (const float*)dpsi, (float*)acc, (float*)dx, (float*)nxt, n, k);
+          SC4_LAUNCH_CHECK();
+        } else {
+          SC4_STENCIL(N, bve_tlm_stage_kernel, T, N, sc, s, (T)g.h, qbase<T>(g) + row, pbase<T>(g) + row,
+                      cur, dpsi, acc, dx, nxt, n);
+        }
       }
     }
   }
@@ -1144,7 +1322,13 @@ int bve_adj(const BveGeom& g, const T* W, int ldw, int k, T* Out, int ldo, void*
         const T* kap = K[(3 - s) & 1];
         T* knext = K[(4 - s) & 1];
         size_t row = (size_t)(4 * (t - 1 - base) + s) * n;
-        SC4_STENCIL(N, bve_adj_jac_kernel, T, N, sc, qbase<T>(g) + row, kap, t12, n);
+        if (sizeof(T) == 4 && N >= 64 && k > 2) {
+          bve_adj_jac_d2_kernel<<<sgrid<float, 64>(N, (k + 1) / 2), kTileThreads, 0, st>>>(
+              N, sc, (const float*)(qbase<T>(g) + row), (const float*)kap, (float*)t12, n, k);
+          SC4_LAUNCH_CHECK();
+        } else {
+          SC4_STENCIL(N, bve_adj_jac_kernel, T, N, sc, qbase<T>(g) + row, kap, t12, n);
+        }
         SC4_TRY(fft2_apply<T, T, T, T>(g, k, t12, (int)n, t12, (int)n, (const T*)nullptr, 0, g.poisson,
                                        cbuf, st));
         SC4_STENCIL(N, bve_adj_stage_kernel, T, N, sc, s, h, pbase<T>(g) + row, kap, t12, th, lam,
