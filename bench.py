@@ -277,9 +277,13 @@ def bve_arm(args):
     nbytes = BVE_PASSES_PER_STEP * wl.n * 4 * wl.n_steps * k
     gn = None
     if not args.no_gn_step:
-        # SketchPrecA set-up: adaptive RandSVD from l0 = k, growing by k/2 to eps_sk = 1.01
-        gn = gn_step(torch, g, prob, wl, dev, sketch={"method": "randsvd", "l": k, "adaptive": True,
-                                                      "l_hat": k // 2, "eps_sk": 1.01})
+        if wl.n_checkpoints:
+            # 1024^2 set-up: Nystrom sketch of the block size (k = 512)
+            sk = {"method": "nystrom", "l": k}
+        else:
+            # SketchPrecA set-up: adaptive RandSVD from l0 = k, growing by k/2 to eps_sk = 1.01
+            sk = {"method": "randsvd", "l": k, "adaptive": True, "l_hat": k // 2, "eps_sk": 1.01}
+        gn = gn_step(torch, g, prob, wl, dev, sketch=sk)
     peak = measured_hbm_gbs()
     out = {"metric": METRIC, "value": k / t, "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,

@@ -111,9 +111,9 @@ class Problem:
         if model == _abi.MODEL_BVE2D:
             d.nx = d.ny = int(grid)
             d.forcing_amp, d.forcing_k = float(forcing_amp), int(forcing_k)
-            d.n_checkpoints = int(n_checkpoints)
         else:
             d.nx, d.ny = int(n), 1
+        d.n_checkpoints = int(n_checkpoints)
         d.nu, d.dt, d.n_steps = float(nu), float(dt), int(n_steps)
         d.n_obs_times = int(obs_idx.shape[0])
         d.n_obs = int(obs_idx.shape[1])

@@ -1210,18 +1210,53 @@ static int n_segments(const BveGeom& g) {
   return g.ckpt_every > 0 ? (g.Nsteps + g.ckpt_every - 1) / g.ckpt_every : 1;
 }
 
-// With checkpointing: recompute the stage states of segment j from its
-// checkpoint into the segment buffers (the precision the sweep of type T reads).
-// The same kernels in the same order as the FWD give bit-identical states.
+// FP32 RK4 steps [t0, t1) of the FWD from the FP32 state at the start of ws
+// (laid out as x, acc, two stage buffers, complex FFT buffer), storing the stage
+// states q_s, psi_s at row 4 (t - t0) + s of q32 / p32.
+static int fwd_steps_f32(const BveGeom& g, void* ws, int t0, int t1, float* q32, float* p32,
+                         cudaStream_t st) {
+  const int N = g.N;
+  const size_t n = (size_t)N * N;
+  float* x = reinterpret_cast<float*>(ws);
+  float* acc = x + n;
+  float* S[2] = {acc + n, acc + 2 * n};
+  void* cbuf = acc + 3 * n;
+  StencilConsts sc = consts(g);
+  const int kz = 1;
+  for (int t = t0; t < t1; ++t) {
+    for (int s = 0; s < 4; ++s) {
+      const float* Xs = (s == 0) ? x : S[(s - 1) & 1];
+      float* nxt = (s < 3) ? S[s & 1] : nullptr;
+      const size_t row = (size_t)(4 * (t - t0) + s) * n;
+      SC4_TRY(fft2_apply<float, float, float, float>(g, 1, Xs, (int)n, p32 + row, (int)n,
+                                                     (const float*)nullptr, 0, g.poisson, cbuf, st));
+      SC4_TRY(copy_fields<float>(n, Xs, q32 + row, st));
+      SC4_STENCIL(N, bve_fwd_stage_kernel, float, N, sc, s, (float)g.h, Xs, p32 + row, acc, x, nxt);
+    }
+  }
+  return SC4DVAR_OK;
+}
+
+// With checkpointing: recompute the stage states of segment j from its FP64
+// checkpoint into the segment buffers, in the precision of the sweep that reads
+// them. FP64 sweeps: the FWD's own kernels in the FWD's order, so the states
+// are bit-identical to stored ones. FP32 sweeps: FP32 steps from the rounded
+// checkpoint (a segment spans few steps, so the states agree with the rounded
+// FP64 ones to FP32 accuracy); the TLM and the ADJ recompute the same states,
+// so they stay exact transposes of each other.
 template <typename T>
 static int recompute_segment(const BveGeom& g, int j, cudaStream_t st) {
   if (g.ckpt_every == 0) return SC4DVAR_OK;
   const size_t n = (size_t)g.N * g.N;
   const Segment sg = segment_of(g, j);
-  SC4_TRY(copy_fields<double>(n, g.ckpt + (size_t)j * n, reinterpret_cast<double*>(g.rws), st));
-  const bool f64 = sizeof(T) == 8;
-  return fwd_steps(g, g.rws, sg.t0, sg.t1, f64 ? g.q64 : nullptr, f64 ? g.p64 : nullptr,
-                   f64 ? nullptr : g.q32, f64 ? nullptr : g.p32, nullptr, nullptr, nullptr, false, st);
+  if constexpr (sizeof(T) == 4) {
+    SC4_TRY(d2f(n, g.ckpt + (size_t)j * n, reinterpret_cast<float*>(g.rws), st));
+    return fwd_steps_f32(g, g.rws, sg.t0, sg.t1, g.q32, g.p32, st);
+  } else {
+    SC4_TRY(copy_fields<double>(n, g.ckpt + (size_t)j * n, reinterpret_cast<double*>(g.rws), st));
+    return fwd_steps(g, g.rws, sg.t0, sg.t1, g.q64, g.p64, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     false, st);
+  }
 }
 
 template <typename T>

@@ -1,9 +1,11 @@
 """Checkpointed barotropic vorticity sweeps and the autograd cost.
 
 With n_checkpoints = c the FWD keeps only the FP64 state every L = ceil(N / c)
-steps and every sweep recomputes one segment of stage states at a time. The
-recompute runs the FWD's kernels in the FWD's order, so every result must be
-bit-identical to the stored-trajectory run. The autograd cost (forward = FWD,
+steps and every sweep recomputes one segment of stage states at a time. FP64
+sweeps recompute with the FWD's kernels in the FWD's order, so their results
+must be bit-identical to the stored-trajectory run; FP32 sweeps recompute in
+FP32 from the rounded checkpoint and agree to FP32 accuracy (and stay exact
+transposes of each other: the FP32 dot test). The autograd cost (forward = FWD,
 backward = the adjoint sweep, Eq. 4dvar_gradient) is checked against the FP64
 oracle at 64^2 and, at the 1024^2 / 256-step / 16-checkpoint size, against
 central differences of J and the adjoint dot test (the oracle is too slow there)."""
@@ -53,11 +55,18 @@ def test_checkpointed_equals_full(small, c):
     assert J0 == J1 and torch.equal(d0, d1)
     assert torch.equal(full.gradient(), ck.gradient())
     X = torch.tensor(np.random.default_rng(c).standard_normal((3, SMALL.n)), device="cuda")
-    for prec, dt in ((g.FP64, torch.float64), (g.FP32, torch.float32)):
-        Xp = X.to(dt)
-        assert torch.equal(full.tlm_block(Xp, prec=prec), ck.tlm_block(Xp, prec=prec))
-        assert torch.equal(full.gn_hessian_apply_block(Xp, prec=prec),
-                           ck.gn_hessian_apply_block(Xp, prec=prec))
+    assert torch.equal(full.tlm_block(X, prec=g.FP64), ck.tlm_block(X, prec=g.FP64))
+    assert torch.equal(full.gn_hessian_apply_block(X, prec=g.FP64), ck.gn_hessian_apply_block(X, prec=g.FP64))
+    Xf = X.float()
+    for fn in (lambda p: p.tlm_block(Xf, prec=g.FP32), lambda p: p.gn_hessian_apply_block(Xf, prec=g.FP32)):
+        a, b = fn(full).double().cpu().numpy(), fn(ck).double().cpu().numpy()
+        assert rel(b, a) <= 1e-5
+    # the recomputed FP32 states are shared by the TLM and the ADJ: exact transposes
+    W = torch.tensor(np.random.default_rng(c + 1).standard_normal((2, SMALL.m)), device="cuda").float()
+    V = Xf[:2]
+    lhs = torch.sum(ck.tlm_block(V, prec=g.FP32).double() * W.double()).item()
+    rhs = torch.sum(V.double() * ck.adj_block(W, prec=g.FP32).double()).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
 def test_autograd_matches_oracle_and_differences(small):
