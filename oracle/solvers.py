@@ -24,7 +24,7 @@ import dataclasses
 
 import numpy as np
 
-from . import philox, sketch
+from . import linesearch, philox, sketch
 
 STREAM_SKETCH = 100
 STREAM_KAPPA = 200
@@ -85,6 +85,10 @@ class GNOptions:
     pcg_tol: float = 1e-6
     pcg_maxit: int | None = None
     seed: int = 20240128
+    line_search: bool = False     # strong-Wolfe step length instead of alpha = 1
+    ls_c1: float = 1e-4
+    ls_c2: float = 0.9
+    ls_alpha1: float = 1.0        # first trial step
 
 
 def build_sketch(prob, o: GNOptions, k: int):
@@ -125,9 +129,14 @@ def gauss_newton(prob, v0, o: GNOptions):
     info = []
     lr = None
     g0 = None
+    carry = None   # (J, g) at v from the last line-search evaluation
     for k in range(o.iters):
-        J = prob.set_iterate(v)
-        g = prob.gradient()
+        if carry is None:
+            J = prob.set_iterate(v)
+            g = prob.gradient()
+        else:
+            J, g = carry
+            carry = None
         gn = float(np.max(np.abs(g)))
         g0 = gn if g0 is None else g0
         rec = {"k": k, "J": J, "g_inf": gn, "sketched": False, "l": 0,
@@ -154,6 +163,22 @@ def gauss_newton(prob, v0, o: GNOptions):
         else:
             dv, its, relres, st = pcg(prob.hvp, -g, P, o.pcg_tol, o.pcg_maxit)
             rec.update(pcg_its=its, relres=relres, status=st)
-        v = v + dv
+        alpha = 1.0
+        if o.line_search:
+            last = {}
+
+            def phi(a, v=v, dv=dv):
+                Ja = prob.set_iterate(v + a * dv)
+                ga = prob.gradient()
+                last["v"] = (a, Ja, ga)
+                return Ja, float(ga @ dv)
+
+            res = linesearch.strong_wolfe(phi, J, float(g @ dv), o.ls_alpha1, o.ls_c1, o.ls_c2)
+            if res.status != linesearch.NOT_DESCENT:
+                alpha = res.alpha
+            rec.update(alpha=alpha, ls_evals=res.evals, ls_status=res.status)
+            if res.last and "v" in last and last["v"][0] == alpha:
+                carry = (last["v"][1], last["v"][2])
+        v = v + alpha * dv
         info.append(rec)
     return v, info
