@@ -148,6 +148,13 @@ typedef struct {
     sc4dvar_sketch_opts sketch;   /* method NONE = Prec_Gamma                      */
     double eps_re;         /* reuse tolerance (Eq. condtext2); adaptive only       */
     sc4dvar_pcg_opts pcg;
+    int line_search;       /* 0: full steps (alpha = 1); 1: strong-Wolfe step length
+                              (bracketing + zoom with cubic interpolation, Nocedal &
+                              Wright Algs. 3.5 / 3.6; the paper uses a Moré-Thuente
+                              search, Sec. 5). Each trial step costs one FWD and one
+                              gradient (ADJ); the last trial's state is reused.      */
+    double ls_c1, ls_c2;   /* sufficient decrease / curvature constants, 0<c1<c2<1 */
+    double ls_alpha1;      /* first trial step (> 0)                               */
 } sc4dvar_gn_opts;
 
 #define SC4DVAR_GN_MAX_ITERS 64
@@ -160,6 +167,10 @@ typedef struct {
     int sketched[SC4DVAR_GN_MAX_ITERS];    /* 1 if a new sketch was built          */
     int rank[SC4DVAR_GN_MAX_ITERS];        /* sketch size in use                   */
     double kappa_re[SC4DVAR_GN_MAX_ITERS]; /* reuse estimate (0 when not computed) */
+    double alpha[SC4DVAR_GN_MAX_ITERS];    /* step length taken                    */
+    int ls_evals[SC4DVAR_GN_MAX_ITERS];    /* line-search trial steps              */
+    int ls_status[SC4DVAR_GN_MAX_ITERS];   /* 0 ok, 1 not a descent direction (full
+                                              step taken), 2 trial budget spent   */
 } sc4dvar_gn_info;
 
 /* Counters in the paper's accounting (Sec. 5, Tables 3-5): a Hessian product
@@ -282,7 +293,8 @@ int sc4dvar_sketchsolv(sc4dvar_precond_t P, const double* g_dev, double* dv_dev,
 
 /* Gauss-Newton from v_inout (overwritten with the final iterate): per iteration
  * FWD, gradient, sketch (every iteration when fixed; when adaptive, the last
- * sketch is reused while kappa_re < eps_re, Sec. 3.2), PCG, v += dv.
+ * sketch is reused while kappa_re < eps_re, Sec. 3.2), PCG, v += alpha dv with
+ * alpha = 1 or a strong-Wolfe step (opts->line_search).
  * Synchronizes. info may be NULL. */
 int sc4dvar_gauss_newton(sc4dvar_problem_t p, const sc4dvar_gn_opts* opts, double* v_inout_dev,
                          sc4dvar_gn_info* info, void* stream);

@@ -265,16 +265,19 @@ class Problem:
 
     def gauss_newton(self, v, iters=3, method="none", l=20, adaptive=False, l2=0, l_hat=0,
                      l_max=0, eps_sk=1.01, eps_re=10.0, tol=1e-6, maxit=0, prec=FP64, refine=2,
-                     gtol=0.0, seed=20240128, stream=None):
+                     gtol=0.0, seed=20240128, line_search=False, ls_c1=1e-4, ls_c2=0.9,
+                     ls_alpha1=1.0, stream=None):
         """Gauss-Newton in place on v (float64, (n,)); returns the per-iteration record."""
         so = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed, 0, prec)
-        o = _abi.GnOpts(iters, gtol, so, eps_re, _abi.PcgOpts(tol, maxit, prec, refine))
+        o = _abi.GnOpts(iters, gtol, so, eps_re, _abi.PcgOpts(tol, maxit, prec, refine), int(line_search),
+                        ls_c1, ls_c2, ls_alpha1)
         info = _abi.GnInfo()
         check(lib.sc4dvar_gauss_newton(self.h, C.byref(o), _ptr(v), C.byref(info), _stream(stream)))
         k = info.iters_done
         return [{"J": info.J[i], "g_inf": info.g_inf[i], "pcg_its": info.pcg_its[i],
                  "relres": info.relres[i], "sketched": bool(info.sketched[i]),
-                 "rank": info.rank[i], "kappa_re": info.kappa_re[i]} for i in range(k)]
+                 "rank": info.rank[i], "kappa_re": info.kappa_re[i], "alpha": info.alpha[i],
+                 "ls_evals": info.ls_evals[i], "ls_status": info.ls_status[i]} for i in range(k)]
 
     def counters(self):
         c = _abi.Counters()

@@ -65,7 +65,8 @@ class PcgInfo(C.Structure):
 
 class GnOpts(C.Structure):
     _fields_ = [("iters", C.c_int), ("gtol", C.c_double), ("sketch", SketchOpts),
-                ("eps_re", C.c_double), ("pcg", PcgOpts)]
+                ("eps_re", C.c_double), ("pcg", PcgOpts), ("line_search", C.c_int),
+                ("ls_c1", C.c_double), ("ls_c2", C.c_double), ("ls_alpha1", C.c_double)]
 
 
 class GnInfo(C.Structure):
@@ -75,6 +76,8 @@ class GnInfo(C.Structure):
         ("pcg_its", C.c_int * GN_MAX_ITERS), ("relres", C.c_double * GN_MAX_ITERS),
         ("sketched", C.c_int * GN_MAX_ITERS), ("rank", C.c_int * GN_MAX_ITERS),
         ("kappa_re", C.c_double * GN_MAX_ITERS),
+        ("alpha", C.c_double * GN_MAX_ITERS), ("ls_evals", C.c_int * GN_MAX_ITERS),
+        ("ls_status", C.c_int * GN_MAX_ITERS),
     ]
 
 

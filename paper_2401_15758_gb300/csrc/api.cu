@@ -1309,24 +1309,125 @@ int sc4dvar_sketchsolv(sc4dvar_precond_t pc, const double* g, double* dv, void* 
   return axpby<double, double>(pc->n, 0.0, dv, -1.0, dv, S(stream));
 }
 
+// ------------------------------------------------------------------ line search
+// Strong-Wolfe step length along dv from v (bracketing and zoom of Nocedal &
+// Wright, Algs. 3.5 / 3.6, cubic interpolation kept 10 % inside the bracket,
+// else bisection; values equal to within rounding leave the decision to the
+// derivative). phi(a) = J(v + a dv) by a FWD, phi'(a) = g(v + a dv)^T dv by the
+// gradient. On return, g holds the gradient at the last trial point and
+// `last` says whether that point is the accepted step.
+namespace {
+constexpr int kLsOk = 0, kLsNotDescent = 1, kLsMaxEvals = 2;
+
+bool cubic_min(double a, double fa, double da, double b, double fb, double db, double* out) {
+  if (a == b) return false;
+  const double d1 = da + db - 3.0 * (fa - fb) / (a - b);
+  const double disc = d1 * d1 - da * db;
+  if (disc < 0.0) return false;
+  const double d2 = std::copysign(std::sqrt(disc), b - a);
+  const double den = db - da + 2.0 * d2;
+  if (den == 0.0) return false;
+  *out = b - (b - a) * (db + d2 - d1) / den;
+  return true;
+}
+
+struct LsResult {
+  double alpha = 1.0, phi = 0.0;
+  int evals = 0, status = kLsOk;
+  bool last = false;
+};
+}  // namespace
+
+static int line_search(Prob* P, const double* v, const double* dv, double* vt, double* g, double phi0,
+                       double dphi0, double alpha1, double c1, double c2, LsResult* out, cudaStream_t st) {
+  const int n = P->n;
+  const double alpha_max = 10.0, eps = std::ldexp(1.0, -52);
+  const int max_evals = 30;
+  LsResult r;
+  if (!(dphi0 < 0.0)) {
+    r.alpha = alpha1;
+    r.status = kLsNotDescent;
+    *out = r;
+    return SC4DVAR_OK;
+  }
+  auto ev = [&](double a, double* f, double* d) -> int {
+    ++r.evals;
+    SC4_TRY(copy_block<double, double>(n, 1, v, n, vt, n, st));
+    SC4_TRY(axpby<double, double>(n, a, dv, 1.0, vt, st));
+    SC4_TRY(fwd_run(P, vt, f, nullptr, st));
+    SC4_TRY(gradient_run(P, g, st));
+    SC4_TRY(vdot<double, double>(n, g, dv, P->scal.as<double>(), P->part.as<double>(), st));
+    return host_scalar(P, d, st);
+  };
+  auto finish = [&](double a, double f, int status, bool last) {
+    r.alpha = a;
+    r.phi = f;
+    r.status = status;
+    r.last = last;
+    *out = r;
+    return SC4DVAR_OK;
+  };
+  auto zoom = [&](double lo, double flo, double dlo, double hi, double fhi, double dhi) -> int {
+    while (r.evals < max_evals) {
+      const double width = hi - lo;
+      double a;
+      const double lo_b = std::min(lo, hi), hi_b = std::max(lo, hi), pad = 0.1 * std::fabs(width);
+      if (!cubic_min(lo, flo, dlo, hi, fhi, dhi, &a) || !(lo_b + pad <= a && a <= hi_b - pad))
+        a = 0.5 * (lo + hi);
+      double f, d;
+      SC4_TRY(ev(a, &f, &d));
+      const bool flat = std::fabs(f - flo) <= 16.0 * eps * std::max(std::fabs(f), std::fabs(flo));
+      if (f > phi0 + c1 * a * dphi0 || (f >= flo && !flat)) {
+        hi = a; fhi = f; dhi = d;
+      } else {
+        if (std::fabs(d) <= -c2 * dphi0) return finish(a, f, kLsOk, true);
+        if (d * (hi - lo) >= 0.0) { hi = lo; fhi = flo; dhi = dlo; }
+        lo = a; flo = f; dlo = d;
+      }
+    }
+    return finish(lo, flo, kLsMaxEvals, false);
+  };
+  double a_prev = 0.0, f_prev = phi0, d_prev = dphi0, a = alpha1;
+  bool first = true;
+  while (r.evals < max_evals) {
+    double f, d;
+    SC4_TRY(ev(a, &f, &d));
+    if (f > phi0 + c1 * a * dphi0 || (!first && f >= f_prev)) return zoom(a_prev, f_prev, d_prev, a, f, d);
+    if (std::fabs(d) <= -c2 * dphi0) return finish(a, f, kLsOk, true);
+    if (d >= 0.0) return zoom(a, f, d, a_prev, f_prev, d_prev);
+    a_prev = a; f_prev = f; d_prev = d;
+    a = std::min(2.0 * a, alpha_max);
+    if (a == a_prev) return finish(a, f, kLsMaxEvals, true);
+    first = false;
+  }
+  return finish(a_prev, f_prev, kLsMaxEvals, false);
+}
+
 int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* v_io,
                          sc4dvar_gn_info* info, void* stream) {
   SC4_ARG(P && o && v_io, "null argument");
   SC4_ARG(o->iters >= 1 && o->iters <= SC4DVAR_GN_MAX_ITERS, "iters");
+  SC4_ARG(!o->line_search || (o->ls_c1 > 0 && o->ls_c1 < o->ls_c2 && o->ls_c2 < 1 && o->ls_alpha1 > 0),
+          "line search constants: 0 < c1 < c2 < 1, alpha1 > 0");
   cudaStream_t st = S(stream);
   const int n = P->n;
   if (info) std::memset(info, 0, sizeof(*info));
   Buf gb;
-  SC4_TRY(gb.ensure((size_t)2 * n * sizeof(double)));
+  SC4_TRY(gb.ensure((size_t)3 * n * sizeof(double)));
   double* g = gb.as<double>();
   double* dv = g + n;
+  double* vt = dv + n;
   Prec* pc = nullptr;
   double g0 = 0;
   int rc = SC4DVAR_OK;
+  bool carry = false;  // J and g at v_io come from the last line-search trial
+  double J = 0.0;
   for (int k = 0; k < o->iters; ++k) {
-    double J;
-    if ((rc = fwd_run(P, v_io, &J, nullptr, st))) break;
-    if ((rc = gradient_run(P, g, st))) break;
+    if (!carry) {
+      if ((rc = fwd_run(P, v_io, &J, nullptr, st))) break;
+      if ((rc = gradient_run(P, g, st))) break;
+    }
+    carry = false;
     double ginf;
     if ((rc = vamax(n, g, P->scal.as<double>(), P->part.as<double>(), st))) break;
     if ((rc = host_scalar(P, &ginf, st))) break;
@@ -1365,7 +1466,26 @@ int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* 
       info->pcg_its[k] = pi.iterations;
       info->relres[k] = pi.relres;
     }
-    if ((rc = axpby<double, double>(n, 1.0, dv, 1.0, v_io, st))) break;
+    double alpha = 1.0;
+    if (o->line_search) {
+      // phi'(0) = g^T dv with g = -b
+      double gdv;
+      if ((rc = vdot<double, double>(n, g, dv, P->scal.as<double>(), P->part.as<double>(), st))) break;
+      if ((rc = host_scalar(P, &gdv, st))) break;
+      LsResult ls;
+      if ((rc = line_search(P, v_io, dv, vt, g, J, -gdv, o->ls_alpha1, o->ls_c1, o->ls_c2, &ls, st))) break;
+      if (ls.status != kLsNotDescent) alpha = ls.alpha;
+      if (info) {
+        info->ls_evals[k] = ls.evals;
+        info->ls_status[k] = ls.status;
+      }
+      if (ls.last && ls.status != kLsNotDescent) {
+        carry = true;
+        J = ls.phi;
+      }
+    }
+    if (info) info->alpha[k] = alpha;
+    if ((rc = axpby<double, double>(n, alpha, dv, 1.0, v_io, st))) break;
   }
   cudaStreamSynchronize(st);
   precond_free(pc);

@@ -150,3 +150,26 @@ def test_adaptive_reuse_gauss_newton_matches_oracle():
         assert abs(a["J"] - b["J"]) <= 1e-9 * abs(b["J"])
         if b["kappa_re"] is not None:
             assert abs(a["kappa_re"] - b["kappa_re"]) <= 1e-8 * b["kappa_re"]
+
+
+@pytest.mark.parametrize("alpha1", [1.0, 3.0])
+def test_gauss_newton_line_search_matches_oracle(alpha1):
+    """Strong-Wolfe GN steps (alpha1 = 3 overshoots, so the bracketing and
+    zoom phases run): cost, step length and trial count per iteration and the
+    final iterate against the oracle's line search."""
+    from oracle import solvers
+    wl = si.burgers_workload("burgers_n128")
+    prob, ref = make_pair(wl)
+    v = torch.zeros(wl.n, dtype=torch.float64, device="cuda")
+    rec = prob.gauss_newton(v, iters=3, method="randsvd", l=20, tol=1e-10, line_search=True,
+                            ls_alpha1=alpha1)
+    vr, info = solvers.gauss_newton(ref, np.zeros(wl.n),
+                                    solvers.GNOptions(iters=3, method="randsvd", l=20, pcg_tol=1e-10,
+                                                      line_search=True, ls_alpha1=alpha1))
+    for a, b in zip(rec, info):
+        assert abs(a["J"] - b["J"]) <= 1e-9 * abs(b["J"])
+        assert a["ls_evals"] == b["ls_evals"] and a["ls_status"] == b["ls_status"]
+        assert abs(a["alpha"] - b["alpha"]) <= 1e-8 * abs(b["alpha"])
+    if alpha1 != 1.0:
+        assert rec[0]["ls_evals"] > 1
+    assert rel(v.cpu().numpy(), vr) <= 1e-7
