@@ -8,7 +8,7 @@ phase of Nocedal & Wright, Numerical Optimization (2nd ed.), Algorithms 3.5 and
 Hermite interpolant of the bracket ends (their Eq. 3.59), kept at least 10 % of
 the bracket away from either end (else bisection). Where the two values
 compared in the zoom phase agree to within a few units of rounding, the
-derivative decides instead (this build's reading: the published algorithm
+derivative decides instead (a reading: the published algorithm
 assumes exact function values).
 
 phi(alpha) = J(v + alpha p) and phi'(alpha) = g(v + alpha p)^T p. A returned
