@@ -113,3 +113,29 @@ def test_prior_multiplier_every_grid(N):
     X = np.random.default_rng(N).standard_normal((3, wl.n))
     Y = prob.prior_sqrt_apply(torch.tensor(X, device="cuda")).cpu().numpy()
     assert rel(Y, bve.apply_symbol_2d(sym, X.T, N).T) <= 1e-12
+
+
+def test_full_window_256_sampled_columns():
+    """bve_n256 at full size (256^2, 200 RK4 steps, m = 131 080) in the launch
+    configuration the benchmark times (one FP32 block of k = 256 directions):
+    two sampled columns (the first; the second lane of the last direction pair)
+    against the oracle's FP64 Hessian product of the same columns."""
+    import paper_2401_15758_gb300 as g
+    from oracle import workload
+    wl = si.bve_workload("bve_n256")
+    assert (wl.N, wl.n_steps, wl.k) == (256, 200, 256)
+    draws = si.bve_draws(wl)
+    ref = workload.bve_problem(wl, draws)
+    prob = g.Problem.from_bve_workload(wl, draws)
+    prob.set_background(torch.tensor(ref.xb, device="cuda"))
+    prob.set_observations(torch.tensor(ref.y.reshape(-1), device="cuda"))
+    prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
+    ref.set_iterate(np.zeros(wl.n))
+    X = si.gaussian_matrix(wl.seed, wl.k, wl.n, stream=23)
+    H = prob.gn_hessian_apply_block(torch.tensor(X, device="cuda", dtype=torch.float32), prec=g.FP32)
+    cols = [0, wl.k - 1]
+    Hr = ref.hvp(X[cols].T).T
+    for j, c in enumerate(cols):
+        err = rel(H[c].double().cpu().numpy(), Hr[j])
+        print(f"column {c}: relative error {err:.3e}")
+        assert err <= 1e-5
