@@ -25,8 +25,9 @@ from . import rk4
 
 class FourDVar:
     def __init__(self, model, h, n_steps, obs_steps, obs_idx, sigma_obs,
-                 prior_sqrt, xb=None, y=None):
+                 prior_sqrt, xb=None, y=None, tableau=rk4.RK4):
         self.model = model
+        self.tab = tableau
         self.h = float(h)
         self.N = int(n_steps)
         self.obs_steps = np.asarray(obs_steps, dtype=np.int64)
@@ -50,7 +51,7 @@ class FourDVar:
         """FWD sweep: the full trajectory x_0 .. x_N (list of (n,) arrays)."""
         xs = [np.array(x0, dtype=np.float64)]
         for _ in range(self.N):
-            xs.append(rk4.fwd_step(self.model, xs[-1], self.h))
+            xs.append(rk4.fwd_step(self.model, xs[-1], self.h, self.tab))
         return xs
 
     def observe(self, traj):
@@ -75,7 +76,7 @@ class FourDVar:
         dx = np.array(dx0, dtype=np.float64)
         out = np.zeros((self.n_t, self.n_o) + dx.shape[1:])
         for t in range(self.N):
-            dx = rk4.tlm_step(self.model, self.traj[t], dx, self.h)
+            dx = rk4.tlm_step(self.model, self.traj[t], dx, self.h, self.tab)
             i = self._obs_at.get(t + 1)
             if i is not None:
                 out[i] = dx[self.obs_idx[i]] / self.sigma
@@ -90,7 +91,7 @@ class FourDVar:
             i = self._obs_at.get(t)
             if i is not None:
                 np.add.at(lam, self.obs_idx[i], Wt[i] / self.sigma)
-            lam = rk4.adj_step(self.model, self.traj[t - 1], lam, self.h)
+            lam = rk4.adj_step(self.model, self.traj[t - 1], lam, self.h, self.tab)
         return lam
 
     def A(self, X):

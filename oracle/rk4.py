@@ -9,7 +9,10 @@ RK method with coefficients a_ij, b_i applied to x' = f(x):
   ADJ      kappa_i = h b_i lam' + h sum_{j>i} a_ji theta_j,  theta_i = F_i^T kappa_i,
            lam = lam' + sum_i theta_i
 with F_i = f'(X_i). The ADJ step is the exact transpose of the TLM step. The
-tableau is classic RK4: a21 = a32 = 1/2, a43 = 1, b = (1/6, 1/3, 1/3, 1/6).
+default tableau is classic RK4: a21 = a32 = 1/2, a43 = 1, b = (1/6, 1/3, 1/3,
+1/6). RK3_TVD is the third-order total-variation-diminishing scheme of the
+paper's experiments (Sec. 5.1, 5.2; Gottlieb & Shu) in Butcher form: a21 = 1,
+a31 = a32 = 1/4, b = (1/6, 1/6, 2/3).
 
 ``model`` is any object with rhs(u), jvp(U, d) and vjp(U, w); blocks of k
 directions are (n, k) arrays and the base stage state U is (n,).
@@ -24,10 +27,17 @@ A = np.array([[0.0, 0.0, 0.0, 0.0],
               [0.0, 0.0, 1.0, 0.0]])
 B = np.array([1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0])
 S = 4
+RK4 = (A, B)
+RK3_TVD = (np.array([[0.0, 0.0, 0.0],
+                     [1.0, 0.0, 0.0],
+                     [0.25, 0.25, 0.0]]),
+           np.array([1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0]))
 
 
-def stages(model, x, h):
-    """Base stage states X_1..X_4 and slopes k_1..k_4 of one step from x."""
+def stages(model, x, h, tab=RK4):
+    """Base stage states X_1..X_S and slopes k_1..k_S of one step from x."""
+    A, B = tab
+    S = len(B)
     X, K = [], []
     for i in range(S):
         Xi = x.copy()
@@ -39,16 +49,20 @@ def stages(model, x, h):
     return X, K
 
 
-def fwd_step(model, x, h):
-    _, K = stages(model, x, h)
+def fwd_step(model, x, h, tab=RK4):
+    A, B = tab
+    S = len(B)
+    _, K = stages(model, x, h, tab)
     out = x.copy()
     for i in range(S):
         out = out + h * B[i] * K[i]
     return out
 
 
-def tlm_step(model, x, dx, h):
-    X, _ = stages(model, x, h)
+def tlm_step(model, x, dx, h, tab=RK4):
+    A, B = tab
+    S = len(B)
+    X, _ = stages(model, x, h, tab)
     dK = []
     for i in range(S):
         dXi = dx.copy()
@@ -62,8 +76,10 @@ def tlm_step(model, x, dx, h):
     return out
 
 
-def adj_step(model, x, lam_next, h):
-    X, _ = stages(model, x, h)
+def adj_step(model, x, lam_next, h, tab=RK4):
+    A, B = tab
+    S = len(B)
+    X, _ = stages(model, x, h, tab)
     theta = [None] * S
     for i in reversed(range(S)):
         kap = h * B[i] * lam_next

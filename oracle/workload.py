@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import burgers, fourdvar, prior
+from . import burgers, burgers_dirichlet, fourdvar, prior, rk4
 
 
 def burgers_problem(wl, draws):
@@ -39,4 +39,18 @@ def bve_problem(wl, draws):
     prob.y = prob.observe(truth) + draws["sigma_obs"] * draws["xi_o"]
     prob.xb = draws["x_true0"] + psq(draws["xi_b"])
     prob.symbol = sym
+    return prob
+
+
+def paper_burgers_problem(wl, draws):
+    """The Dirichlet / RK3-TVD Burgers experiment of Sec. 5.1 (same twin
+    construction as burgers_problem)."""
+    model = burgers_dirichlet.BurgersDirichlet(wl.n, wl.nu)
+    psq = burgers_dirichlet.inv_helmholtz_sqrt(wl.n, wl.prior_a, wl.prior_b)
+    prob = fourdvar.FourDVar(model, wl.dt, wl.n_steps, wl.obs_steps, draws["obs_idx"],
+                             wl.sigma_obs, psq, tableau=rk4.RK3_TVD)
+    truth = prob.forward(draws["x_true0"])
+    prob.x_true_traj = truth
+    prob.y = prob.observe(truth) + wl.sigma_obs * draws["xi_o"]
+    prob.xb = draws["x_true0"] + psq(draws["xi_b"])
     return prob

@@ -297,6 +297,63 @@ def bve_draws(wl: BVEWorkload) -> dict:
     }
 
 
+@dataclasses.dataclass(frozen=True)
+class PaperBurgersWorkload:
+    """The Burgers experiment of Sec. 5.1 (Experiments 1.1 / 1.2): Dirichlet
+    boundaries on (0, 1), n interior points, nu = 0.1, RK3-TVD step 2.5e-5,
+    n_t = 20 observation times 0.01 apart (400 steps), n_o = 15 observed states,
+    R = 0.01 I, Gamma = (0.5 I - 500 Delta*)^{-2}, truth sin(pi x), l = 15."""
+    name: str = "burgers_paper"
+    n: int = 399
+    nu: float = 0.1
+    dt: float = 2.5e-5
+    obs_every: int = 400
+    n_obs_times: int = 20
+    n_obs: int = 15
+    sigma_obs: float = 0.1
+    prior_a: float = 0.5
+    prior_b: float = 500.0
+    k: int = 15
+    gn_iters: int = 3
+    pcg_tol: float = 1e-9
+    seed: int = DEFAULT_SEED
+
+    @property
+    def n_steps(self) -> int:
+        return self.obs_every * self.n_obs_times
+
+    @property
+    def obs_steps(self) -> np.ndarray:
+        return np.arange(1, self.n_obs_times + 1, dtype=np.int32) * self.obs_every
+
+    @property
+    def m(self) -> int:
+        return self.n_obs_times * self.n_obs
+
+    @property
+    def x(self) -> np.ndarray:
+        return np.arange(1, self.n + 1) / (self.n + 1)
+
+
+def paper_burgers_workload(**overrides) -> PaperBurgersWorkload:
+    base = PaperBurgersWorkload()
+    return dataclasses.replace(base, **overrides) if overrides else base
+
+
+def paper_burgers_draws(wl: PaperBurgersWorkload) -> dict:
+    """Truth sin(pi x); n_o sites evenly spaced over the interior (index
+    round((i + 1)(n + 1)/(n_o + 1)) - 1, the same at every time); background and
+    observation noise from the seeded streams."""
+    sites = np.array([int(round((i + 1) * (wl.n + 1) / (wl.n_obs + 1))) - 1 for i in range(wl.n_obs)],
+                     dtype=np.int32)
+    return {
+        "x_true0": np.sin(np.pi * wl.x),
+        "xi_b": _rng(wl.seed, STREAM_BACKGROUND).standard_normal(wl.n),
+        "xi_o": _rng(wl.seed, STREAM_OBS_NOISE).standard_normal((wl.n_obs_times, wl.n_obs)),
+        "obs_idx": np.tile(sites, (wl.n_obs_times, 1)),
+    }
+
+
 def burgers_batch(count: int = 64, seed: int = DEFAULT_SEED):
     """Uneven batch of Burgers windows: n from {512, ..., 8192}, N_out from
     {100, 200, 400} and k from {16, 32, 64}, drawn per problem from seed + p;
