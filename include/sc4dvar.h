@@ -53,12 +53,27 @@ extern "C" {
 /* ---- enumerations ------------------------------------------------------- */
 #define SC4DVAR_MODEL_BURGERS1D 1      /* periodic 1D viscous Burgers, Sec. 5.1  */
 #define SC4DVAR_MODEL_BVE2D     2      /* doubly periodic barotropic vorticity   */
+#define SC4DVAR_MODEL_BURGERS1D_DIRICHLET 3 /* 1D viscous Burgers on (0, 1) with
+                                          u(0) = u(1) = 0 (the paper's set-up, Sec.
+                                          5.1): nx = n interior points x_j = j/(n+1),
+                                          3..1024, ny = 1                        */
+
+/* Time integrators (sc4dvar_problem_desc.integrator). The TLM and ADJ are the
+   discrete tangent-linear and adjoint models of the chosen scheme. */
+#define SC4DVAR_RK4     0              /* classic RK4 (all models)                */
+#define SC4DVAR_RK3_TVD 1              /* third-order TVD Runge-Kutta (Dirichlet
+                                          Burgers; the paper's experiments)     */
 
 #define SC4DVAR_FP64 0
 #define SC4DVAR_FP32 1
 
 #define SC4DVAR_PRIOR_SYMBOL    0      /* caller gives the Fourier symbol of Gamma^{1/2} */
 #define SC4DVAR_PRIOR_SE        1      /* sigma_b^2 exp(-d^2/(2 L^2)), periodic distance */
+#define SC4DVAR_PRIOR_DIRICHLET_INV_HELMHOLTZ 3 /* Gamma^{1/2} = (a I - b Delta*)^{-1},
+                                          Delta* = tridiag(1, -2, 1) with zero
+                                          boundary values: a = prior_sigma,
+                                          b = prior_length (Dirichlet Burgers; the
+                                          paper's Gamma = (0.5 I - 500 Delta*)^{-2}) */
 #define SC4DVAR_PRIOR_INV_HELMHOLTZ 2  /* Gamma^{1/2} = c (I - ell^2 Lap)^{-1} on the 2D grid:
                                           c = prior_sigma, ell = prior_length (BVE)         */
 
@@ -112,6 +127,7 @@ typedef struct {
                               identical to c = 0. Burgers: must be 0.              */
     /* BVE (Sec. 5.2, doubly periodic form): q_t = -J_A(psi, q) + nu Lap_h q + F,
        psi = Lap^{-1} q (spectral), J_A Arakawa's Jacobian, Lap_h five-point. */
+    int integrator;        /* SC4DVAR_RK4 (default) or SC4DVAR_RK3_TVD               */
 } sc4dvar_problem_desc;
 
 /* Sketch options (Sec. 3.1). */

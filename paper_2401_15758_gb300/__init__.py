@@ -103,7 +103,7 @@ class Problem:
 
     def __init__(self, *, n, nu, dt, n_steps, obs_steps, obs_idx, sigma_obs,
                  prior_sigma=None, prior_length=None, prior_symbol=None, model=MODEL_BURGERS1D,
-                 grid=None, forcing_amp=0.0, forcing_k=0, n_checkpoints=0):
+                 grid=None, forcing_amp=0.0, forcing_k=0, n_checkpoints=0, integrator=0):
         obs_steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
         obs_idx = np.ascontiguousarray(obs_idx, dtype=np.int32)
         d = _abi.ProblemDesc()
@@ -120,8 +120,12 @@ class Problem:
         d.obs_steps = obs_steps.ctypes.data_as(C.POINTER(C.c_int))
         d.obs_idx = obs_idx.ctypes.data_as(C.POINTER(C.c_int))
         d.sigma_obs = float(sigma_obs)
+        d.integrator = int(integrator)
         if model == _abi.MODEL_BVE2D:
             d.prior_kind = _abi.PRIOR_INV_HELMHOLTZ
+            d.prior_sigma, d.prior_length = float(prior_sigma), float(prior_length)
+        elif model == _abi.MODEL_BURGERS1D_DIRICHLET:
+            d.prior_kind = _abi.PRIOR_DIRICHLET_INV_HELMHOLTZ
             d.prior_sigma, d.prior_length = float(prior_sigma), float(prior_length)
         elif prior_symbol is not None:
             sym = np.ascontiguousarray(prior_symbol, dtype=np.float64)
@@ -155,6 +159,15 @@ class Problem:
                    prior_sigma=draws["prior_c"], prior_length=draws["prior_ell"],
                    model=_abi.MODEL_BVE2D, grid=wl.N, forcing_amp=wl.forcing_amp,
                    forcing_k=wl.forcing_k)
+
+    @classmethod
+    def from_paper_burgers_workload(cls, wl, draws):
+        """The Burgers experiment of Sec. 5.1: Dirichlet boundaries, n interior
+        points, RK3-TVD, prior Gamma^{1/2} = (a I - b Delta*)^{-1}."""
+        return cls(n=wl.n, nu=wl.nu, dt=wl.dt, n_steps=wl.n_steps, obs_steps=wl.obs_steps,
+                   obs_idx=draws["obs_idx"], sigma_obs=wl.sigma_obs, prior_sigma=wl.prior_a,
+                   prior_length=wl.prior_b, model=_abi.MODEL_BURGERS1D_DIRICHLET,
+                   integrator=_abi.RK3_TVD)
 
     def close(self):
         if getattr(self, "h", None):

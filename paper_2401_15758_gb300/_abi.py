@@ -19,6 +19,9 @@ ERR_STATE = -8
 
 MODEL_BURGERS1D = 1
 MODEL_BVE2D = 2
+MODEL_BURGERS1D_DIRICHLET = 3
+RK4, RK3_TVD = 0, 1
+PRIOR_DIRICHLET_INV_HELMHOLTZ = 3
 FP64 = 0
 FP32 = 1
 PRIOR_SYMBOL = 0
@@ -43,6 +46,7 @@ class ProblemDesc(C.Structure):
         ("prior_kind", C.c_int), ("prior_sigma", C.c_double), ("prior_length", C.c_double),
         ("prior_symbol", C.POINTER(C.c_double)),
         ("forcing_amp", C.c_double), ("forcing_k", C.c_int), ("n_checkpoints", C.c_int),
+        ("integrator", C.c_int),
     ]
 
 

@@ -13,6 +13,7 @@
 #include "fft.cuh"
 #include "model.cuh"
 #include "problem.cuh"
+#include "dirichlet.cuh"
 
 namespace sc4 {
 
@@ -142,13 +143,21 @@ template <> const double* traj_of<double>(Prob* P) { return P->traj64; }
 template <> const float* traj_of<float>(Prob* P) { return P->traj32; }
 
 static bool is_bve(const Prob* P) { return P->model == SC4DVAR_MODEL_BVE2D; }
+static bool is_dir(const Prob* P) { return P->model == SC4DVAR_MODEL_BURGERS1D_DIRICHLET; }
 
-// Y = Gamma^{1/2} X (+ Z) for k columns: the 1D circulant (FFT) or the 2D
-// spectral multiplier of the model's grid.
+// Y = Gamma^{1/2} X (+ Z) for k columns: the 1D circulant (FFT), the 2D
+// spectral multiplier of the model's grid, or the tridiagonal inverse of the
+// Dirichlet prior.
 template <typename TI, typename TO, typename TZ>
 static int prior_any(Prob* P, int k, const TI* X, int ldx, TO* Y, int ldy, const TZ* Z, int ldz,
                      cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
+  if (is_dir(P)) {
+    SC4_TRY(P->wDir.ensure((size_t)P->n * k * sizeof(double)));
+    P->dir.work = P->wDir.as<double>();
+    P->dir.work_cols = (int)(P->wDir.bytes / ((size_t)P->n * sizeof(double)));
+    return dir_prior_apply<TI, TO, TZ>(P->dir, k, X, ldx, Y, ldy, Z, ldz, st);
+  }
   if (!is_bve(P)) return prior_apply<TI, TO, TZ>(P->n, k, X, ldx, Y, ldy, Z, ldz, P->sym, P->tw, st);
   constexpr bool f32 = sizeof(TI) == 4 && sizeof(TO) == 4;
   using R = typename std::conditional<f32, float, double>::type;
@@ -159,6 +168,7 @@ static int prior_any(Prob* P, int k, const TI* X, int ldx, TO* Y, int ldy, const
 // W = R^{-1/2} O_i M_i U for all i (TLM sweep of k columns)
 template <typename T>
 static int model_tlm(Prob* P, const T* U, int ldu, int k, T* W, int ldw, cudaStream_t st) {
+  if (is_dir(P)) return dir_tlm<T>(P->dir, traj_of<T>(P), U, ldu, k, W, ldw, st);
   if (!is_bve(P)) return burgers_tlm<T>(P->geom, traj_of<T>(P), U, ldu, k, W, ldw, st);
   SC4_TRY(P->wBve.ensure(bve_sweep_ws_bytes(P->bve, k, sizeof(T))));
   return bve_tlm<T>(P->bve, U, ldu, k, W, ldw, P->wBve.p, st);
@@ -167,6 +177,7 @@ static int model_tlm(Prob* P, const T* U, int ldu, int k, T* W, int ldw, cudaStr
 // L = sum_i M_i^T O_i^T R^{-1/2} W_i (ADJ sweep of k columns)
 template <typename T>
 static int model_adj(Prob* P, const T* W, int ldw, int k, T* L, int ldl, cudaStream_t st) {
+  if (is_dir(P)) return dir_adj<T>(P->dir, traj_of<T>(P), W, ldw, k, L, ldl, st);
   if (!is_bve(P)) return burgers_adj<T>(P->geom, traj_of<T>(P), W, ldw, k, L, ldl, st);
   SC4_TRY(P->wBve.ensure(bve_sweep_ws_bytes(P->bve, k, sizeof(T))));
   return bve_adj<T>(P->bve, W, ldw, k, L, ldl, P->wBve.p, st);
@@ -877,7 +888,9 @@ static int fwd_run(Prob* P, const double* v, double* J_host, double* d_out, cuda
   const int n = P->n, m = P->m;
   if (v != P->v) SC4_CUDA(cudaMemcpyAsync(P->v, v, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SC4_TRY(prior_any<double, double, double>(P, 1, P->v, n, P->x0, n, P->xb, n, st));
-  if (is_bve(P)) {
+  if (is_dir(P)) {
+    SC4_TRY(dir_fwd(P->dir, P->x0, P->traj64, P->traj32, P->y, P->d, nullptr, nullptr, st));
+  } else if (is_bve(P)) {
     SC4_TRY(P->wBve.ensure(std::max(bve_fwd_ws_bytes(P->bve), bve_sweep_ws_bytes(P->bve, 1, 8))));
     SC4_TRY(bve_fwd(P->bve, P->x0, true, P->y, P->d, nullptr, nullptr, P->wBve.p, st));
   } else {
@@ -972,9 +985,21 @@ long long sc4dvar_launch_count(void) { return g_launches.load(); }
 
 int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out) {
   SC4_ARG(d && out, "null descriptor or output");
-  SC4_ARG(d->model == SC4DVAR_MODEL_BURGERS1D || d->model == SC4DVAR_MODEL_BVE2D, "unknown model");
+  SC4_ARG(d->model == SC4DVAR_MODEL_BURGERS1D || d->model == SC4DVAR_MODEL_BVE2D ||
+              d->model == SC4DVAR_MODEL_BURGERS1D_DIRICHLET,
+          "unknown model");
   const bool bve = d->model == SC4DVAR_MODEL_BVE2D;
-  if (bve) {
+  const bool dirm = d->model == SC4DVAR_MODEL_BURGERS1D_DIRICHLET;
+  SC4_ARG(d->integrator == SC4DVAR_RK4 || (dirm && d->integrator == SC4DVAR_RK3_TVD),
+          "integrator: RK4, or RK3-TVD for the Dirichlet Burgers model");
+  if (dirm) {
+    SC4_ARG(d->nx >= 3 && d->nx <= 1024 && d->ny == 1, "Dirichlet Burgers: n interior points in [3, 1024]");
+    SC4_ARG(d->prior_kind == SC4DVAR_PRIOR_DIRICHLET_INV_HELMHOLTZ && d->prior_sigma > 0 &&
+                d->prior_length >= 0,
+            "Dirichlet Burgers prior: SC4DVAR_PRIOR_DIRICHLET_INV_HELMHOLTZ with a = prior_sigma > 0, "
+            "b = prior_length >= 0");
+    SC4_ARG(d->n_checkpoints == 0, "checkpointing covers the BVE model (n_checkpoints must be 0)");
+  } else if (bve) {
     SC4_ARG(d->nx == d->ny && d->nx >= 16 && d->nx <= 1024 && (d->nx & (d->nx - 1)) == 0,
             "BVE grid must be N x N with N a power of two in [16, 1024]");
     SC4_ARG(d->prior_kind == SC4DVAR_PRIOR_INV_HELMHOLTZ && d->prior_sigma > 0 && d->prior_length >= 0,
@@ -996,7 +1021,7 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   }
   for (long i = 0; i < (long)d->n_obs_times * d->n_obs; ++i)
     SC4_ARG(d->obs_idx[i] >= 0 && d->obs_idx[i] < n, "obs_idx out of range");
-  SC4_ARG(bve || d->prior_kind == SC4DVAR_PRIOR_SE ||
+  SC4_ARG(bve || dirm || d->prior_kind == SC4DVAR_PRIOR_SE ||
               (d->prior_kind == SC4DVAR_PRIOR_SYMBOL && d->prior_symbol),
           "prior");
   SC4_ARG(d->prior_kind != SC4DVAR_PRIOR_SE || (d->prior_sigma > 0 && d->prior_length > 0),
@@ -1054,8 +1079,9 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   }
   if (cudaMalloc(&P->obs_of_step, oos.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&P->obs_idx, (size_t)P->m * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&P->sym, (bve ? 1 : n) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&P->tw, (bve ? 1 : n / 2) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&P->sym, (bve || dirm ? 1 : n) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->tw, (bve || dirm ? 1 : n / 2) * sizeof(double2)) != cudaSuccess ||
+      (dirm && cudaMalloc(&P->dir_cp, 2 * (size_t)n * sizeof(double)) != cudaSuccess) ||
       cudaMalloc(&P->xb, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->y, P->m * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->v, n * sizeof(double)) != cudaSuccess ||
@@ -1086,7 +1112,7 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   P->geom.n_o = P->n_o;
   P->geom.obs_of_step = P->obs_of_step;
   P->geom.obs_idx = P->obs_idx;
-  P->geom.fold32 = (!bve && packed_f32_supported(n)) ? 1 : 0;
+  P->geom.fold32 = (!bve && !dirm && packed_f32_supported(n)) ? 1 : 0;
   if (bve) {
     BveGeom& b = P->bve;
     b.N = d->nx;
@@ -1120,7 +1146,42 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   } else if ((rc = fft_make_twiddles(n, P->tw, 0))) {
     return fail(rc);
   }
-  if (bve) {
+  if (dirm) {
+    DirGeom& g = P->dir;
+    g.n = n;
+    g.N = P->N;
+    g.n_o = P->n_o;
+    g.h = P->h;
+    g.nu = P->nu;
+    g.sigma = P->sigma;
+    g.obs_of_step = P->obs_of_step;
+    g.obs_idx = P->obs_idx;
+    for (int i = 0; i < 4; ++i) {
+      g.b[i] = 0.0;
+      for (int j = 0; j < 4; ++j) g.a[i][j] = 0.0;
+    }
+    if (d->integrator == SC4DVAR_RK3_TVD) {  // Butcher form of the TVD scheme
+      g.S = 3;
+      g.a[1][0] = 1.0;
+      g.a[2][0] = 0.25;
+      g.a[2][1] = 0.25;
+      g.b[0] = 1.0 / 6.0;
+      g.b[1] = 1.0 / 6.0;
+      g.b[2] = 2.0 / 3.0;
+    } else {
+      g.S = 4;
+      g.a[1][0] = 0.5;
+      g.a[2][1] = 0.5;
+      g.a[3][2] = 1.0;
+      g.b[0] = g.b[3] = 1.0 / 6.0;
+      g.b[1] = g.b[2] = 1.0 / 3.0;
+    }
+    g.cp = P->dir_cp;
+    g.den = P->dir_cp + n;
+    g.work = nullptr;
+    g.work_cols = 0;
+    if ((rc = dir_setup(g, d->prior_sigma, d->prior_length, 0))) return fail(rc);
+  } else if (bve) {
     // prior handled by the 2D multiplier
   } else if (d->prior_kind == SC4DVAR_PRIOR_SE) {
     if ((rc = fft_se_symbol(n, d->prior_sigma, d->prior_length, kClampRel, P->tw, P->sym, 0)))
@@ -1143,7 +1204,8 @@ int sc4dvar_problem_destroy(sc4dvar_problem_t P) {
   if (!P) return SC4DVAR_OK;
   cudaFree(P->obs_of_step); cudaFree(P->obs_idx); cudaFree(P->sym); cudaFree(P->tw);
   cudaFree(P->xb); cudaFree(P->y); cudaFree(P->v); cudaFree(P->x0); cudaFree(P->d);
-  cudaFree(P->traj64); cudaFree(P->traj32);
+  cudaFree(P->traj64); cudaFree(P->traj32); cudaFree(P->dir_cp);
+  P->wDir.release();
   cudaFree(P->bve_tw64); cudaFree(P->bve_tw32); cudaFree(P->bve_poisson); cudaFree(P->bve_prior);
   cudaFree(P->bve_tabc64); cudaFree(P->bve_tabc32);
   cudaFree(P->bve_q64); cudaFree(P->bve_p64); cudaFree(P->bve_q32); cudaFree(P->bve_p32);
@@ -1187,6 +1249,7 @@ int sc4dvar_prior_sqrt_apply(sc4dvar_problem_t P, const double* X, int ldx, int 
 
 int sc4dvar_prior_symbol(sc4dvar_problem_t P, double* symbol_host) {
   SC4_ARG(P && symbol_host, "null argument");
+  SC4_ARG(!is_dir(P), "the Dirichlet prior has no Fourier symbol");
   if (is_bve(P)) {
     SC4_CUDA(cudaMemcpy(symbol_host, P->bve.prior, P->n * sizeof(double), cudaMemcpyDeviceToHost));
     return SC4DVAR_OK;
@@ -1197,6 +1260,7 @@ int sc4dvar_prior_symbol(sc4dvar_problem_t P, double* symbol_host) {
 
 int sc4dvar_forecast(sc4dvar_problem_t P, const double* x0, double* obs, double* xN, void* stream) {
   SC4_ARG(P && x0 && obs, "null argument");
+  if (is_dir(P)) return dir_fwd(P->dir, x0, nullptr, nullptr, nullptr, nullptr, obs, xN, S(stream));
   if (is_bve(P)) {
     SC4_TRY(P->wBve.ensure(std::max(bve_fwd_ws_bytes(P->bve), P->wBve.bytes)));
     return bve_fwd(P->bve, x0, false, nullptr, nullptr, obs, xN, P->wBve.p, S(stream));

@@ -5,6 +5,7 @@
 #include "common.cuh"
 #include "model.cuh"
 #include "bve.cuh"
+#include "dirichlet.cuh"
 #include <vector>
 
 namespace sc4 {
@@ -61,6 +62,10 @@ struct sc4dvar_problem_s {
   float* bve_tabc32 = nullptr;
   double *bve_q64 = nullptr, *bve_p64 = nullptr;
   float *bve_q32 = nullptr, *bve_p32 = nullptr;
+  // Dirichlet Burgers problems: geometry, prior elimination tables, prior work columns
+  sc4::DirGeom dir{};
+  double* dir_cp = nullptr;
+  sc4::Buf wDir;
   double* bve_ckpt = nullptr;  // checkpoint states (checkpointing only)
   void* bve_rws = nullptr;     // segment recompute workspace (checkpointing only)
   sc4::Buf wBve, wCplx;

@@ -1,0 +1,116 @@
+"""Parity of the CUDA Dirichlet / RK3-TVD Burgers path (the Burgers experiment
+of Sec. 5.1) with the FP64 oracle, through the C ABI: prior, FWD, cost,
+gradient, TLM / ADJ / Hessian blocks (FP64 1e-10, FP32 1e-5), the dot test, the
+full 399-point / 8000-step window on sampled columns, and a Gauss-Newton run
+with sketched PCG and the strong-Wolfe line search."""
+import numpy as np
+import pytest
+
+import sc4dvar_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from test_gpu_burgers import rel  # noqa: E402
+
+
+def make(wl):
+    import paper_2401_15758_gb300 as g
+    from oracle import workload
+    draws = si.paper_burgers_draws(wl)
+    ref = workload.paper_burgers_problem(wl, draws)
+    prob = g.Problem.from_paper_burgers_workload(wl, draws)
+    prob.set_background(torch.tensor(ref.xb, device="cuda"))
+    prob.set_observations(torch.tensor(ref.y.reshape(-1), device="cuda"))
+    return prob, ref
+
+
+SMALL = si.paper_burgers_workload(n=31, obs_every=20, n_obs_times=5, n_obs=7)
+
+
+@pytest.fixture(scope="module")
+def small():
+    prob, ref = make(SMALL)
+    v = 0.3 * np.random.default_rng(3).standard_normal(SMALL.n)
+    Jr = ref.set_iterate(v)
+    Jg = prob.fwd(torch.tensor(v, device="cuda"))
+    return prob, ref, v, Jr, Jg
+
+
+def test_prior_forecast_cost_gradient(small):
+    prob, ref, v, Jr, Jg = small
+    X = np.random.default_rng(1).standard_normal((3, SMALL.n))
+    assert rel(prob.prior_sqrt_apply(torch.tensor(X, device="cuda")).cpu().numpy(), ref.prior_sqrt(X.T).T) <= 1e-13
+    obs, xN = prob.forecast(torch.tensor(ref.x_true_traj[0], device="cuda"))
+    assert rel(obs.cpu().numpy(), ref.observe(ref.x_true_traj).reshape(-1)) <= 1e-12
+    assert rel(xN.cpu().numpy(), ref.x_true_traj[-1]) <= 1e-12
+    assert abs(Jg - Jr) <= 1e-11 * abs(Jr)
+    assert rel(prob.gradient().cpu().numpy(), ref.gradient()) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_blocks_match_oracle(small, prec):
+    import paper_2401_15758_gb300 as g
+    prob, ref, *_ = small
+    p = g.FP64 if prec == "fp64" else g.FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((3, SMALL.n))
+    Wm = rng.standard_normal((3, SMALL.m))
+    A = prob.tlm_block(torch.tensor(X, device="cuda", dtype=dt), prec=p).double().cpu().numpy()
+    At = prob.adj_block(torch.tensor(Wm, device="cuda", dtype=dt), prec=p).double().cpu().numpy()
+    H = prob.gn_hessian_apply_block(torch.tensor(X, device="cuda", dtype=dt), prec=p).double().cpu().numpy()
+    Ar, Atr, Hr = ref.A(X.T).T, ref.At(Wm.T).T, ref.hvp(X.T).T
+    for j in range(3):
+        assert rel(A[j], Ar[j]) <= tol
+        assert rel(At[j], Atr[j]) <= tol
+        assert rel(H[j], Hr[j]) <= tol
+
+
+def test_dot_test(small):
+    prob, *_ = small
+    rng = np.random.default_rng(6)
+    X = torch.tensor(rng.standard_normal((2, SMALL.n)), device="cuda")
+    W = torch.tensor(rng.standard_normal((2, SMALL.m)), device="cuda")
+    a = torch.sum(prob.tlm_block(X) * W).item()
+    b = torch.sum(X * prob.adj_block(W)).item()
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_full_window_sampled_columns():
+    """n = 399, 8000 RK3 steps, m = 300: two Hessian-product columns of a k = 15
+    block (the paper's sketch size) in FP64 and FP32 against the oracle."""
+    import paper_2401_15758_gb300 as g
+    wl = si.paper_burgers_workload()
+    prob, ref = make(wl)
+    prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
+    ref.set_iterate(np.zeros(wl.n))
+    X = si.gaussian_matrix(wl.seed, wl.k, wl.n, stream=29)
+    H64 = prob.gn_hessian_apply_block(torch.tensor(X, device="cuda"), prec=g.FP64).cpu().numpy()
+    H32 = prob.gn_hessian_apply_block(torch.tensor(X, device="cuda", dtype=torch.float32),
+                                      prec=g.FP32).double().cpu().numpy()
+    cols = [0, wl.k - 1]
+    Hr = ref.hvp(X[cols].T).T
+    for j, c in enumerate(cols):
+        assert rel(H64[c], Hr[j]) <= 1e-10
+        assert rel(H32[c], Hr[j]) <= 1e-5
+
+
+def test_gauss_newton_with_line_search_matches_oracle():
+    """RandSVD (l = 15) sketched PCG with the strong-Wolfe step on the paper's
+    grid over a 5-time window: costs, step lengths and the final iterate."""
+    from oracle import solvers
+    wl = si.paper_burgers_workload(n_obs_times=5)
+    prob, ref = make(wl)
+    v = torch.zeros(wl.n, dtype=torch.float64, device="cuda")
+    rec = prob.gauss_newton(v, iters=2, method="randsvd", l=wl.k, tol=1e-9, line_search=True)
+    vr, info = solvers.gauss_newton(ref, np.zeros(wl.n),
+                                    solvers.GNOptions(iters=2, method="randsvd", l=wl.k, pcg_tol=1e-9,
+                                                      line_search=True))
+    for a, b in zip(rec, info):
+        assert abs(a["J"] - b["J"]) <= 1e-9 * abs(b["J"])
+        assert abs(a["alpha"] - b["alpha"]) <= 1e-8
+        assert abs(a["pcg_its"] - b["pcg_its"]) <= 1
+    assert rel(v.cpu().numpy(), vr) <= 1e-7
