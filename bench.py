@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-gn-step", action="store_true", help="skip the time-to-solution part")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256", "bve_n1024", "burgers_batch64"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256", "bve_n1024", "burgers_batch64", "burgers_paper"],
                     help="the Burgers block (default) or the barotropic vorticity block")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
@@ -380,6 +380,83 @@ def batch_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def paper_arm(args):
+    """The Burgers experiment of Sec. 5.1 (Dirichlet, RK3-TVD, n = 399, 8000 steps,
+    15 sites, 20 times): 3 GN iterations with l = l1 = 15, l2 = 31, PCG to 1e-9,
+    strong-Wolfe steps, FP64, for Prec_Gamma and the three SketchPrec variants;
+    PDE-solve counts and times next to the counts the paper prints (Table 3).
+    The block product of the sketch size (k = 15, FP64) is the timed step."""
+    import torch
+    import paper_2401_15758_gb300 as g
+    import sc4dvar_inputs as si
+    dev = torch.device("cuda", 0)
+    wl = si.paper_burgers_workload()
+    d = si.paper_burgers_draws(wl)
+
+    def problem():
+        p = g.Problem.from_paper_burgers_workload(wl, d)
+        xt = torch.tensor(d["x_true0"], device=dev)
+        obs, _ = p.forecast(xt)
+        p.set_observations(obs + wl.sigma_obs * torch.tensor(d["xi_o"].reshape(-1), device=dev))
+        p.set_background(xt + p.prior_sqrt_apply(torch.tensor(d["xi_b"], device=dev)))
+        return p
+
+    paper = {}
+    gold = os.path.join(ROOT, "tests", "golden", "paper_counts.txt")
+    with open(gold) as f:
+        for line in f:
+            if line.startswith("T3 "):
+                t, meth, *vals = line.split()
+                paper[meth] = [None if v == "-" else int(v) for v in vals]
+    names = {"none": "Prec_Gamma", "randsvd": "SketchPrec_RandSVD", "nystrom": "SketchPrec_Nystrom",
+             "singleview": "SketchPrec_SingleView"}
+    rows = {}
+    for method in ("none", "randsvd", "nystrom", "singleview"):
+        p = problem()
+        p.counters_reset()
+        v = torch.zeros(wl.n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rec = p.gauss_newton(v, iters=3, method=method, l=wl.k, l2=2 * wl.k + 1, tol=1e-9, gtol=1e-6,
+                             line_search=True)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        c = p.counters()
+        ours = {"pcg_its": sum(r["pcg_its"] for r in rec), "tlm_off": c["tlm_offline"],
+                "adj_off": c["adj_offline"], "fwd": c["fwd"], "tlm_on": c["tlm_online"],
+                "adj_on": c["adj_online"], "gn_iters": len(rec), "J_final": rec[-1]["J"],
+                "alphas": [r["alpha"] for r in rec], "seconds": secs}
+        pr = paper.get(names[method])
+        rows[names[method]] = {"ours": ours, "paper": None if pr is None else dict(
+            zip(("pcg_its", "tlm_off", "adj_off", "fwd", "tlm_on", "adj_on"), pr))}
+        p.close()
+    # timed step: FP64 block product of the sketch size
+    p = problem()
+    p.fwd(torch.zeros(wl.n, dtype=torch.float64, device=dev))
+    X = torch.tensor(si.gaussian_matrix(wl.seed, wl.k, wl.n, stream=29), device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        p.gn_hessian_apply_block(X)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p.gn_hessian_apply_block(X)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(e))
+    t = statistics.mean(ms) / 1e3
+    out = {"metric": METRIC, "value": wl.k / t, "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{wl.name}: Dirichlet Burgers n={wl.n}, nu={wl.nu}, RK3-TVD, "
+                                  f"{wl.n_steps} steps, m={wl.m}, block k={wl.k}, FP64",
+                      "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": wl.k},
+           "paper_table3_comparison": rows}
+    print(json.dumps(out), flush=True)
+
+
 def measured_hbm_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -611,6 +688,8 @@ def main():
         bve_arm(args)
     elif args.workload == "burgers_batch64":
         batch_arm(args)
+    elif args.workload == "burgers_paper":
+        paper_arm(args)
     else:
         gpu_arm(args)
 
