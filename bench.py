@@ -383,7 +383,8 @@ def batch_arm(args):
 def paper_arm(args):
     """The Burgers experiment of Sec. 5.1 (Dirichlet, RK3-TVD, n = 399, 8000 steps,
     15 sites, 20 times): 3 GN iterations with l = l1 = 15, l2 = 31, PCG to 1e-9,
-    strong-Wolfe steps, FP64, for Prec_Gamma and the three SketchPrec variants;
+    strong-Wolfe steps, FP64, for Prec_Gamma and the three sketches as PCG
+    preconditioners (SketchPrec) and as direct steps (SketchSolv);
     PDE-solve counts and times next to the counts the paper prints (Table 3).
     The block product of the sketch size (k = 15, FP64) is the timed step."""
     import torch
@@ -408,17 +409,19 @@ def paper_arm(args):
             if line.startswith("T3 "):
                 t, meth, *vals = line.split()
                 paper[meth] = [None if v == "-" else int(v) for v in vals]
-    names = {"none": "Prec_Gamma", "randsvd": "SketchPrec_RandSVD", "nystrom": "SketchPrec_Nystrom",
-             "singleview": "SketchPrec_SingleView"}
+    runs = [("none", "pcg", "Prec_Gamma"), ("randsvd", "pcg", "SketchPrec_RandSVD"),
+            ("nystrom", "pcg", "SketchPrec_Nystrom"), ("singleview", "pcg", "SketchPrec_SingleView"),
+            ("randsvd", "sketchsolv", "SketchSolv_RandSVD"), ("nystrom", "sketchsolv", "SketchSolv_Nystrom"),
+            ("singleview", "sketchsolv", "SketchSolv_SingleView")]
     rows = {}
-    for method in ("none", "randsvd", "nystrom", "singleview"):
+    for method, solve, name in runs:
         p = problem()
         p.counters_reset()
         v = torch.zeros(wl.n, dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rec = p.gauss_newton(v, iters=3, method=method, l=wl.k, l2=2 * wl.k + 1, tol=1e-9, gtol=1e-6,
-                             line_search=True)
+                             line_search=True, solve=solve)
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         c = p.counters()
@@ -426,8 +429,8 @@ def paper_arm(args):
                 "adj_off": c["adj_offline"], "fwd": c["fwd"], "tlm_on": c["tlm_online"],
                 "adj_on": c["adj_online"], "gn_iters": len(rec), "J_final": rec[-1]["J"],
                 "alphas": [r["alpha"] for r in rec], "seconds": secs}
-        pr = paper.get(names[method])
-        rows[names[method]] = {"ours": ours, "paper": None if pr is None else dict(
+        pr = paper.get(name)
+        rows[name] = {"ours": ours, "paper": None if pr is None else dict(
             zip(("pcg_its", "tlm_off", "adj_off", "fwd", "tlm_on", "adj_on"), pr))}
         p.close()
     # timed step: FP64 block product of the sketch size

@@ -171,6 +171,9 @@ typedef struct {
                               gradient (ADJ); the last trial's state is reused.      */
     double ls_c1, ls_c2;   /* sufficient decrease / curvature constants, 0<c1<c2<1 */
     double ls_alpha1;      /* first trial step (> 0)                               */
+    int solve;             /* 0: PCG on (I + H) (SketchPrec / Prec_Gamma);
+                              1: SketchSolv, dv = -(I + H_hat)^{-1} g (Eq. dxsol; needs
+                              a sketch method, no PCG)                             */
 } sc4dvar_gn_opts;
 
 #define SC4DVAR_GN_MAX_ITERS 64

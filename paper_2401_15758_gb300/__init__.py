@@ -279,11 +279,11 @@ class Problem:
     def gauss_newton(self, v, iters=3, method="none", l=20, adaptive=False, l2=0, l_hat=0,
                      l_max=0, eps_sk=1.01, eps_re=10.0, tol=1e-6, maxit=0, prec=FP64, refine=2,
                      gtol=0.0, seed=20240128, line_search=False, ls_c1=1e-4, ls_c2=0.9,
-                     ls_alpha1=1.0, stream=None):
+                     ls_alpha1=1.0, solve="pcg", stream=None):
         """Gauss-Newton in place on v (float64, (n,)); returns the per-iteration record."""
         so = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed, 0, prec)
         o = _abi.GnOpts(iters, gtol, so, eps_re, _abi.PcgOpts(tol, maxit, prec, refine), int(line_search),
-                        ls_c1, ls_c2, ls_alpha1)
+                        ls_c1, ls_c2, ls_alpha1, {"pcg": 0, "sketchsolv": 1}[solve])
         info = _abi.GnInfo()
         check(lib.sc4dvar_gauss_newton(self.h, C.byref(o), _ptr(v), C.byref(info), _stream(stream)))
         k = info.iters_done

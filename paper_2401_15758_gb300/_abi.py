@@ -70,7 +70,8 @@ class PcgInfo(C.Structure):
 class GnOpts(C.Structure):
     _fields_ = [("iters", C.c_int), ("gtol", C.c_double), ("sketch", SketchOpts),
                 ("eps_re", C.c_double), ("pcg", PcgOpts), ("line_search", C.c_int),
-                ("ls_c1", C.c_double), ("ls_c2", C.c_double), ("ls_alpha1", C.c_double)]
+                ("ls_c1", C.c_double), ("ls_c2", C.c_double), ("ls_alpha1", C.c_double),
+                ("solve", C.c_int)]
 
 
 class GnInfo(C.Structure):

@@ -1473,6 +1473,8 @@ int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* 
   SC4_ARG(o->iters >= 1 && o->iters <= SC4DVAR_GN_MAX_ITERS, "iters");
   SC4_ARG(!o->line_search || (o->ls_c1 > 0 && o->ls_c1 < o->ls_c2 && o->ls_c2 < 1 && o->ls_alpha1 > 0),
           "line search constants: 0 < c1 < c2 < 1, alpha1 > 0");
+  SC4_ARG(o->solve == 0 || (o->solve == 1 && o->sketch.method != SC4DVAR_SKETCH_NONE),
+          "solve: 0 (PCG) or 1 (SketchSolv, needs a sketch method)");
   cudaStream_t st = S(stream);
   const int n = P->n;
   if (info) std::memset(info, 0, sizeof(*info));
@@ -1524,11 +1526,17 @@ int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* 
     }
     // b = -g
     if ((rc = axpby<double, double>(n, -1.0, g, 0.0, g, st))) break;
-    sc4dvar_pcg_info pi{};
-    if ((rc = pcg_run(P, pc, g, dv, o->pcg, &pi, st))) break;
-    if (info) {
-      info->pcg_its[k] = pi.iterations;
-      info->relres[k] = pi.relres;
+    if (o->solve == 1) {
+      // SketchSolv (Eq. dxsol): dv = (I + H_hat)^{-1} b, b = -g
+      if ((rc = pc->T.ensure((size_t)std::max(pc->l, 1) * sizeof(double)))) break;
+      if ((rc = woodbury_apply(n, pc->l, 1, pc->V, n, pc->dsc, g, n, dv, n, pc->T.as<double>(), st))) break;
+    } else {
+      sc4dvar_pcg_info pi{};
+      if ((rc = pcg_run(P, pc, g, dv, o->pcg, &pi, st))) break;
+      if (info) {
+        info->pcg_its[k] = pi.iterations;
+        info->relres[k] = pi.relres;
+      }
     }
     double alpha = 1.0;
     if (o->line_search) {

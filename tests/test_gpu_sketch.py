@@ -173,3 +173,23 @@ def test_gauss_newton_line_search_matches_oracle(alpha1):
     if alpha1 != 1.0:
         assert rec[0]["ls_evals"] > 1
     assert rel(v.cpu().numpy(), vr) <= 1e-7
+
+
+@pytest.mark.parametrize("method", ["randsvd", "nystrom", "singleview"])
+def test_gauss_newton_sketchsolv_matches_oracle(method):
+    """SketchSolv GN steps (Eq. dxsol): no PCG, the sketch's Woodbury inverse
+    applied to the gradient; costs and the final iterate against the oracle,
+    and the online counts (no TLM, one ADJ per gradient)."""
+    from oracle import solvers
+    wl = si.burgers_workload("burgers_n128")
+    prob, ref = make_pair(wl)
+    prob.counters_reset()
+    v = torch.zeros(wl.n, dtype=torch.float64, device="cuda")
+    rec = prob.gauss_newton(v, iters=3, method=method, l=20, solve="sketchsolv")
+    vr, info = solvers.gauss_newton(ref, np.zeros(wl.n),
+                                    solvers.GNOptions(iters=3, method=method, l=20, solve="sketchsolv"))
+    for a, b in zip(rec, info):
+        assert abs(a["J"] - b["J"]) <= 1e-9 * abs(b["J"]) and a["pcg_its"] == 0
+    assert rel(v.cpu().numpy(), vr) <= 1e-8
+    c = prob.counters()
+    assert c["tlm_online"] == 0 and c["adj_online"] == 3
