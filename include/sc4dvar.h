@@ -66,6 +66,11 @@ extern "C" {
 
 #define SC4DVAR_FP64 0
 #define SC4DVAR_FP32 1
+#define SC4DVAR_DF64 2   /* FP64-class accuracy (~1e-14 per operation) from double-float
+                            arithmetic on the FP32 pipe: blocks are double in and out,
+                            the sweeps run on (hi, lo) float pairs. Periodic Burgers
+                            only, sc4dvar_gn_hessian_apply_block only; PCG uses it for
+                            the defect-correction residual of periodic Burgers problems. */
 
 #define SC4DVAR_PRIOR_SYMBOL    0      /* caller gives the Fourier symbol of Gamma^{1/2} */
 #define SC4DVAR_PRIOR_SE        1      /* sigma_b^2 exp(-d^2/(2 L^2)), periodic distance */

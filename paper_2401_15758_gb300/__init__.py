@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 
 from . import _abi
-from ._abi import (FP32, FP64, MODEL_BURGERS1D, PRIOR_SE, PRIOR_SYMBOL, SKETCH_NONE,  # noqa: F401
+from ._abi import (DF64, FP32, FP64, MODEL_BURGERS1D, PRIOR_SE, PRIOR_SYMBOL, SKETCH_NONE,  # noqa: F401
                    SKETCH_NYSTROM, SKETCH_RANDSVD, SKETCH_SINGLEVIEW, STREAM_KAPPA, STREAM_PSI,
                    STREAM_SKETCH, Sc4dvarError)
 
@@ -43,7 +43,7 @@ def _stream(stream=None):
 
 def _dtype(prec):
     torch = _torch()
-    return torch.float64 if prec == FP64 else torch.float32
+    return torch.float32 if prec == FP32 else torch.float64
 
 
 class Precond:

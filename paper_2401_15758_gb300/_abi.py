@@ -24,6 +24,7 @@ RK4, RK3_TVD = 0, 1
 PRIOR_DIRICHLET_INV_HELMHOLTZ = 3
 FP64 = 0
 FP32 = 1
+DF64 = 2      # double blocks, double-float sweeps (periodic Burgers Hessian products)
 PRIOR_SYMBOL = 0
 PRIOR_SE = 1
 PRIOR_INV_HELMHOLTZ = 2

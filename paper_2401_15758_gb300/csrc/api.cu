@@ -10,6 +10,7 @@
 #include <vector>
 #include "common.cuh"
 #include "dense.cuh"
+#include "dfloat.cuh"
 #include "fft.cuh"
 #include "model.cuh"
 #include "problem.cuh"
@@ -216,8 +217,49 @@ static int hvp_block(Prob* P, const T* X, int ldx, int k, T* Y, int ldy, int mis
   return SC4DVAR_OK;
 }
 
+// Y = (I + A^T A) X (or A^T A X) for double blocks with double-float sweeps
+// (periodic Burgers): the prior square root in FP64, the TLM / ADJ sweeps on
+// (hi, lo) float pairs over a double-float copy of the FP64 trajectory.
+static int hvp_block_df64(Prob* P, const double* X, int ldx, int k, double* Y, int ldy, int misfit_only,
+                          cudaStream_t st) {
+  const int n = P->n, m = P->m;
+  if (k <= 0) return SC4DVAR_OK;
+  if (!P->traj_df) {
+    if (cudaMalloc(&P->traj_df, (size_t)(P->N + 1) * n * sizeof(dfloat)) != cudaSuccess) {
+      cudaGetLastError();
+      P->traj_df = nullptr;
+      set_error("DF64: allocation of the double-float trajectory failed");
+      return SC4DVAR_ERR_OOM;
+    }
+    P->traj_df_valid = false;
+  }
+  dfloat* traj = reinterpret_cast<dfloat*>(P->traj_df);
+  if (!P->traj_df_valid) {
+    SC4_TRY(to_dfloat(n, P->N + 1, P->traj64, n, traj, n, st));
+    P->traj_df_valid = true;
+  }
+  SC4_TRY(P->wU.ensure((size_t)n * k * sizeof(double)));
+  SC4_TRY(P->wL.ensure((size_t)n * k * sizeof(double)));
+  SC4_TRY(P->wDF.ensure((size_t)(2 * n + m) * k * sizeof(dfloat)));
+  double* U = P->wU.as<double>();
+  double* L = P->wL.as<double>();
+  dfloat* Ud = P->wDF.as<dfloat>();
+  dfloat* Wd = Ud + (size_t)n * k;
+  dfloat* Ld = Wd + (size_t)m * k;
+  SC4_TRY(prior_any<double, double, double>(P, k, X, ldx, U, n, (const double*)nullptr, 0, st));
+  SC4_TRY(to_dfloat(n, k, U, n, Ud, n, st));
+  SC4_TRY(burgers_tlm<dfloat>(P->geom, traj, Ud, n, k, Wd, m, st));
+  SC4_TRY(burgers_adj<dfloat>(P->geom, traj, Wd, m, k, Ld, n, st));
+  SC4_TRY(from_dfloat(n, k, Ld, n, L, n, st));
+  SC4_TRY(prior_any<double, double, double>(P, k, L, n, Y, ldy, misfit_only ? (const double*)nullptr : X, ldx,
+                                            st));
+  count(P, k, k);
+  return SC4DVAR_OK;
+}
+
 // q = (I + H) p for one FP64 vector, operator arithmetic in prec (launches only).
 static int hvp_vec_launch(Prob* P, const double* p, double* q, int prec, cudaStream_t st) {
+  if (prec == SC4DVAR_DF64) return hvp_block_df64(P, p, P->n, 1, q, P->n, 0, st);
   if (prec == SC4DVAR_FP64) return hvp_block<double>(P, p, P->n, 1, q, P->n, 0, st);
   int n = P->n, m = P->m;
   SC4_TRY(P->wU.ensure((size_t)n * sizeof(float)));
@@ -858,8 +900,9 @@ static int pcg_run(Prob* P, Prec* pc, const double* b, double* x, const sc4dvar_
       relres = rel_in * rhs_norm / bnorm;
       break;
     }
-    // FP64 residual of the accumulated solution (counted as one online HVP)
-    SC4_TRY(hvp_vec(P, x, q, SC4DVAR_FP64, st));
+    // FP64-class residual of the accumulated solution (counted as one online
+    // HVP): double-float sweeps for periodic Burgers, FP64 otherwise
+    SC4_TRY(hvp_vec(P, x, q, P->model == SC4DVAR_MODEL_BURGERS1D ? SC4DVAR_DF64 : SC4DVAR_FP64, st));
     SC4_TRY(copy_block<double, double>(n, 1, b, n, rhs, n, st));
     SC4_TRY(axpby<double, double>(n, -1.0, q, 1.0, rhs, st));
     SC4_TRY(vnrm2<double>(n, rhs, sc, part, st));
@@ -897,6 +940,7 @@ static int fwd_run(Prob* P, const double* v, double* J_host, double* d_out, cuda
     SC4_TRY(burgers_fwd<double>(P->geom, P->x0, P->traj64, P->traj32, P->y, P->d, nullptr, nullptr, st));
   }
   P->have_traj = true;
+  P->traj_df_valid = false;
   P->counters.fwd += 1;
   if (d_out) SC4_CUDA(cudaMemcpyAsync(d_out, P->d, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (J_host) {
@@ -1204,7 +1248,8 @@ int sc4dvar_problem_destroy(sc4dvar_problem_t P) {
   if (!P) return SC4DVAR_OK;
   cudaFree(P->obs_of_step); cudaFree(P->obs_idx); cudaFree(P->sym); cudaFree(P->tw);
   cudaFree(P->xb); cudaFree(P->y); cudaFree(P->v); cudaFree(P->x0); cudaFree(P->d);
-  cudaFree(P->traj64); cudaFree(P->traj32); cudaFree(P->dir_cp);
+  cudaFree(P->traj64); cudaFree(P->traj32); cudaFree(P->dir_cp); cudaFree(P->traj_df);
+  P->wDF.release();
   P->wDir.release();
   cudaFree(P->bve_tw64); cudaFree(P->bve_tw32); cudaFree(P->bve_poisson); cudaFree(P->bve_prior);
   cudaFree(P->bve_tabc64); cudaFree(P->bve_tabc32);
@@ -1311,6 +1356,12 @@ int sc4dvar_adj_block(sc4dvar_problem_t P, const void* W, int ldw, int k, void* 
 
 int sc4dvar_gn_hessian_apply_block(sc4dvar_problem_t P, const void* X, int ldx, int k, void* Y,
                                    int ldy, int misfit_only, int prec, void* stream) {
+  if (P && prec == SC4DVAR_DF64) {
+    SC4_ARG(P->model == SC4DVAR_MODEL_BURGERS1D, "SC4DVAR_DF64 needs the periodic Burgers model");
+    SC4_TRY(check_block(P, k, SC4DVAR_FP64));
+    SC4_ARG(ldx >= P->n && ldy >= P->n && (k == 0 || (X && Y)), "leading dimensions / pointers");
+    return hvp_block_df64(P, (const double*)X, ldx, k, (double*)Y, ldy, misfit_only, S(stream));
+  }
   SC4_TRY(check_block(P, k, prec));
   SC4_ARG(ldx >= P->n && ldy >= P->n && (k == 0 || (X && Y)), "leading dimensions / pointers");
   if (prec == SC4DVAR_FP64)

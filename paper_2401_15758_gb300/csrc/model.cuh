@@ -32,6 +32,10 @@ int burgers_fwd(const ModelGeom& g, const T* x0, T* traj, float* traj32, const d
 template <typename T>
 int burgers_tlm(const ModelGeom& g, const T* traj, const T* U0, int ldu, int k, T* W, int ldw,
                 cudaStream_t st);
+struct dfloat;
+// column-major block conversions between double and double-float
+int to_dfloat(int rows, int cols, const double* x, int ldx, dfloat* y, int ldy, cudaStream_t st);
+int from_dfloat(int rows, int cols, const dfloat* x, int ldx, double* y, int ldy, cudaStream_t st);
 template <typename T>
 int burgers_adj(const ModelGeom& g, const T* traj, const T* W, int ldw, int k, T* Out, int ldo,
                 cudaStream_t st);

@@ -51,6 +51,9 @@ struct sc4dvar_problem_s {
   double *xb = nullptr, *y = nullptr, *v = nullptr, *x0 = nullptr, *d = nullptr;
   double* traj64 = nullptr;
   float* traj32 = nullptr;
+  void* traj_df = nullptr;     // double-float copy of traj64 (periodic Burgers, on demand)
+  bool traj_df_valid = false;  // the copy matches the current trajectory
+  sc4::Buf wDF;                // double-float work blocks of the DF64 products
   bool have_traj = false;
   // barotropic vorticity problems: geometry, tables and stored stage states
   sc4::BveGeom bve{};

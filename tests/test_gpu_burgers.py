@@ -177,3 +177,39 @@ def test_register_resident_sweeps_match_oracle(n, n_out, k, prec):
         assert rel(H[j], Hr[j]) <= tol
     g_ = prob.gradient().cpu().numpy()
     assert rel(g_, ref.gradient()) <= 1e-10
+
+
+# Double-float sweeps: double blocks in and out, the TLM / ADJ sweeps on (hi, lo)
+# float pairs (about 48 significant bits), held to the FP64 tolerance.
+DF64_CASES = [
+    # (n, output steps, k)
+    (128, None, 1),     # the small window, one direction
+    (128, None, 6),     # several directions, one CTA each
+    (8192, 20, 2),      # 16-CTA cluster, 512 points per CTA
+    (2048, 20, 5),      # 2 points per thread, odd k
+]
+
+
+@pytest.mark.parametrize("n,n_out,k", DF64_CASES)
+def test_df64_hessian_matches_oracle(n, n_out, k):
+    import paper_2401_15758_gb300 as g
+    kw = {} if n_out is None else {"n": n, "n_out": n_out}
+    wl = si.burgers_workload("burgers_n128" if n == 128 else "burgers_n8192", **kw)
+    prob, ref = make_pair(wl)
+    v = 0.2 * np.random.default_rng(n + 1).standard_normal(wl.n)
+    ref.set_iterate(v)
+    prob.fwd(torch.tensor(v, device="cuda"))
+    X = np.random.default_rng(40 + k).standard_normal((k, wl.n))
+    Xd = torch.tensor(X, device="cuda")
+    H = prob.gn_hessian_apply_block(Xd, prec=g.DF64).cpu().numpy()
+    Hm = prob.gn_hessian_apply_block(Xd, misfit_only=True, prec=g.DF64).cpu().numpy()
+    Hr, Hmr = ref.hvp(X.T).T, ref.misfit_hvp(X.T).T
+    for j in range(k):
+        assert rel(H[j], Hr[j]) <= 1e-10
+        assert rel(Hm[j], Hmr[j]) <= 1e-10
+    # a new FWD refreshes the double-float trajectory
+    v2 = v + 0.1
+    ref.set_iterate(v2)
+    prob.fwd(torch.tensor(v2, device="cuda"))
+    H2 = prob.gn_hessian_apply_block(Xd[:1], prec=g.DF64).cpu().numpy()
+    assert rel(H2[0], ref.hvp(X[:1].T).T[0]) <= 1e-10

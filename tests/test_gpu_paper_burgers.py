@@ -69,6 +69,15 @@ def test_blocks_match_oracle(small, prec):
         assert rel(H[j], Hr[j]) <= tol
 
 
+def test_df64_is_periodic_burgers_only(small):
+    import paper_2401_15758_gb300 as g
+    prob, *_ = small
+    X = torch.zeros((1, SMALL.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(g.Sc4dvarError) as e:
+        prob.gn_hessian_apply_block(X, prec=g.DF64)
+    assert e.value.code == g._abi.ERR_INVALID_ARG
+
+
 def test_dot_test(small):
     prob, *_ = small
     rng = np.random.default_rng(6)
