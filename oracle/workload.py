@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import burgers, burgers_dirichlet, fourdvar, prior, rk4
+from . import burgers, burgers_dirichlet, bve_gyre, fourdvar, prior, rk4
 
 
 def burgers_problem(wl, draws):
@@ -53,4 +53,30 @@ def paper_burgers_problem(wl, draws):
     prob.x_true_traj = truth
     prob.y = prob.observe(truth) + wl.sigma_obs * draws["xi_o"]
     prob.xb = draws["x_true0"] + psq(draws["xi_b"])
+    return prob
+
+
+def gyre_truth0(wl, draws, model=None, psq=None):
+    """Spun-up truth of the double-gyre workload: init_scale Gamma^{1/2} xi_init
+    advanced spin_steps RK3-TVD steps."""
+    model = model or bve_gyre.BVEGyre(wl.nx, wl.re, wl.ro)
+    psq = psq or bve_gyre.inv_helmholtz_sqrt_2d(wl.nx, wl.prior_a, wl.prior_b)
+    x = wl.init_scale * psq(draws["xi_init"])
+    for _ in range(wl.spin_steps):
+        x = rk4.fwd_step(model, x, wl.dt, rk4.RK3_TVD)
+    return x
+
+
+def gyre_problem(wl, draws):
+    """The double-gyre barotropic vorticity experiment of Sec. 5.2 (same twin
+    construction as burgers_problem, truth from gyre_truth0)."""
+    model = bve_gyre.BVEGyre(wl.nx, wl.re, wl.ro)
+    psq = bve_gyre.inv_helmholtz_sqrt_2d(wl.nx, wl.prior_a, wl.prior_b)
+    prob = fourdvar.FourDVar(model, wl.dt, wl.n_steps, wl.obs_steps, draws["obs_idx"],
+                             wl.sigma_obs, psq, tableau=rk4.RK3_TVD)
+    x0 = gyre_truth0(wl, draws, model, psq)
+    truth = prob.forward(x0)
+    prob.x_true_traj = truth
+    prob.y = prob.observe(truth) + wl.sigma_obs * draws["xi_o"]
+    prob.xb = x0 + psq(draws["xi_b"])
     return prob

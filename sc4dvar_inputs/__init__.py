@@ -354,6 +354,95 @@ def paper_burgers_draws(wl: PaperBurgersWorkload) -> dict:
     }
 
 
+@dataclasses.dataclass(frozen=True)
+class GyreWorkload:
+    """The barotropic vorticity experiment of Sec. 5.2: a wind-driven double gyre
+    on (0, 1) x (-1, 1) with psi = omega = 0 on the boundary, Re = 200,
+    Ro = 0.0016, F = sin(pi y). nx x ny interior points, h = 1/(nx + 1),
+    ny = 2 nx + 1 (128 x 257 = 32896 states, h = 0.00775). RK3-TVD step
+    2.45e-4; n_t = 8 observation times 5 steps (about six hours) apart; a
+    16 x 16 sensor grid; R = 361 I; Gamma = (-0.06 Delta*)^{-2}; l = 384.
+
+    The truth is a spun-up state: a small random vorticity field (prior-shaped,
+    init_scale Gamma^{1/2} xi_init) run spin_steps RK3 steps forward by each
+    side's own model."""
+    name: str = "bve_gyre"
+    nx: int = 128
+    re: float = 200.0
+    ro: float = 0.0016
+    dt: float = 2.45e-4
+    obs_every: int = 5
+    n_obs_times: int = 8
+    n_sensors: int = 16          # per dimension
+    sigma_obs: float = 19.0
+    prior_a: float = 0.0
+    prior_b: float = 0.06
+    init_scale: float = 1e-3
+    spin_steps: int = 400
+    k: int = 384
+    pcg_tol: float = 1e-9
+    seed: int = DEFAULT_SEED
+
+    @property
+    def ny(self) -> int:
+        return 2 * self.nx + 1
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def h(self) -> float:
+        return 1.0 / (self.nx + 1)
+
+    @property
+    def n_steps(self) -> int:
+        return self.obs_every * self.n_obs_times
+
+    @property
+    def obs_steps(self) -> np.ndarray:
+        return np.arange(1, self.n_obs_times + 1, dtype=np.int32) * self.obs_every
+
+    @property
+    def n_obs(self) -> int:
+        return self.n_sensors * self.n_sensors
+
+    @property
+    def m(self) -> int:
+        return self.n_obs_times * self.n_obs
+
+
+def gyre_workload(**overrides) -> GyreWorkload:
+    base = GyreWorkload()
+    return dataclasses.replace(base, **overrides) if overrides else base
+
+
+def gyre_sensor_index(wl: GyreWorkload) -> np.ndarray:
+    """Sensor sites of an equally spaced s x s grid: along each axis of m
+    interior points the 1-based indices round((2a + 1)(m + 1) / (2 s)),
+    a = 0..s-1 (symmetric about the centre); flattened row-major (y slow)."""
+    s = wl.n_sensors
+
+    def axis(m):
+        idx = np.array([int(np.floor((2 * a + 1) * (m + 1) / (2.0 * s) + 0.5)) for a in range(s)]) - 1
+        assert np.all(np.diff(idx) > 0) and idx[0] >= 0 and idx[-1] < m
+        return idx
+    ix, iy = axis(wl.nx), axis(wl.ny)
+    return (iy[:, None] * wl.nx + ix[None, :]).reshape(-1).astype(np.int32)
+
+
+def gyre_draws(wl: GyreWorkload) -> dict:
+    """xi_init (shape of the spin-up's initial field), xi_b, xi_o and the sensor
+    sites (the same at every observation time)."""
+    sites = gyre_sensor_index(wl)
+    return {
+        "xi_init": _rng(wl.seed, STREAM_TRUTH).standard_normal(wl.n),
+        "xi_b": _rng(wl.seed, STREAM_BACKGROUND).standard_normal(wl.n),
+        "xi_o": _rng(wl.seed, STREAM_OBS_NOISE).standard_normal((wl.n_obs_times, wl.n_obs)),
+        "obs_idx": np.tile(sites, (wl.n_obs_times, 1)),
+    }
+
+
 def burgers_batch(count: int = 64, seed: int = DEFAULT_SEED):
     """Uneven batch of Burgers windows: n from {512, ..., 8192}, N_out from
     {100, 200, 400} and k from {16, 32, 64}, drawn per problem from seed + p;
