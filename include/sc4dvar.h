@@ -57,12 +57,24 @@ extern "C" {
                                           u(0) = u(1) = 0 (the paper's set-up, Sec.
                                           5.1): nx = n interior points x_j = j/(n+1),
                                           3..1024, ny = 1                        */
+#define SC4DVAR_MODEL_BVE_GYRE  4      /* wind-driven barotropic vorticity in the
+                                          closed basin (0, 1) x (-1, 1) with psi =
+                                          omega = 0 on the boundary (the double-gyre
+                                          set-up of Sec. 5.2): omega_t = -J(psi,
+                                          omega) + Ro^{-1} psi_x + Re^{-1} Lap omega +
+                                          Ro^{-1} sin(pi y), Lap psi = -omega, central
+                                          differences on nx x ny interior points,
+                                          h = 1/(nx+1), ny = 2 nx + 1, nx a power of two
+                                          in [8, 128]; nu = 1/Re, forcing_amp = 1/Ro;
+                                          prior SC4DVAR_PRIOR_DIRICHLET_INV_HELMHOLTZ
+                                          with the five-point Delta*                */
 
 /* Time integrators (sc4dvar_problem_desc.integrator). The TLM and ADJ are the
    discrete tangent-linear and adjoint models of the chosen scheme. */
 #define SC4DVAR_RK4     0              /* classic RK4 (all models)                */
 #define SC4DVAR_RK3_TVD 1              /* third-order TVD Runge-Kutta (Dirichlet
-                                          Burgers; the paper's experiments)     */
+                                          Burgers and the double gyre; the paper's
+                                          experiments)                          */
 
 #define SC4DVAR_FP64 0
 #define SC4DVAR_FP32 1
@@ -75,10 +87,12 @@ extern "C" {
 #define SC4DVAR_PRIOR_SYMBOL    0      /* caller gives the Fourier symbol of Gamma^{1/2} */
 #define SC4DVAR_PRIOR_SE        1      /* sigma_b^2 exp(-d^2/(2 L^2)), periodic distance */
 #define SC4DVAR_PRIOR_DIRICHLET_INV_HELMHOLTZ 3 /* Gamma^{1/2} = (a I - b Delta*)^{-1},
-                                          Delta* = tridiag(1, -2, 1) with zero
-                                          boundary values: a = prior_sigma,
-                                          b = prior_length (Dirichlet Burgers; the
-                                          paper's Gamma = (0.5 I - 500 Delta*)^{-2}) */
+                                          Delta* the unscaled Laplacian stencil with
+                                          zero boundary values (tridiag(1, -2, 1) for
+                                          Dirichlet Burgers, five-point for the
+                                          double gyre): a = prior_sigma, b =
+                                          prior_length (the paper's Gamma = (0.5 I -
+                                          500 Delta*)^{-2} and (-0.06 Delta*)^{-2}) */
 #define SC4DVAR_PRIOR_INV_HELMHOLTZ 2  /* Gamma^{1/2} = c (I - ell^2 Lap)^{-1} on the 2D grid:
                                           c = prior_sigma, ell = prior_length (BVE)         */
 

@@ -111,6 +111,9 @@ class Problem:
         if model == _abi.MODEL_BVE2D:
             d.nx = d.ny = int(grid)
             d.forcing_amp, d.forcing_k = float(forcing_amp), int(forcing_k)
+        elif model == _abi.MODEL_BVE_GYRE:
+            d.nx, d.ny = int(grid), 2 * int(grid) + 1
+            d.forcing_amp = float(forcing_amp)
         else:
             d.nx, d.ny = int(n), 1
         d.n_checkpoints = int(n_checkpoints)
@@ -124,7 +127,7 @@ class Problem:
         if model == _abi.MODEL_BVE2D:
             d.prior_kind = _abi.PRIOR_INV_HELMHOLTZ
             d.prior_sigma, d.prior_length = float(prior_sigma), float(prior_length)
-        elif model == _abi.MODEL_BURGERS1D_DIRICHLET:
+        elif model in (_abi.MODEL_BURGERS1D_DIRICHLET, _abi.MODEL_BVE_GYRE):
             d.prior_kind = _abi.PRIOR_DIRICHLET_INV_HELMHOLTZ
             d.prior_sigma, d.prior_length = float(prior_sigma), float(prior_length)
         elif prior_symbol is not None:
@@ -168,6 +171,16 @@ class Problem:
                    obs_idx=draws["obs_idx"], sigma_obs=wl.sigma_obs, prior_sigma=wl.prior_a,
                    prior_length=wl.prior_b, model=_abi.MODEL_BURGERS1D_DIRICHLET,
                    integrator=_abi.RK3_TVD)
+
+    @classmethod
+    def from_gyre_workload(cls, wl, draws):
+        """The barotropic vorticity experiment of Sec. 5.2: the double gyre in the
+        closed basin (0, 1) x (-1, 1) on nx x (2 nx + 1) interior points, Re, Ro,
+        RK3-TVD, prior Gamma^{1/2} = (a I - b Delta*)^{-1} (five-point Delta*)."""
+        return cls(n=wl.n, nu=1.0 / wl.re, dt=wl.dt, n_steps=wl.n_steps, obs_steps=wl.obs_steps,
+                   obs_idx=draws["obs_idx"], sigma_obs=wl.sigma_obs, prior_sigma=wl.prior_a,
+                   prior_length=wl.prior_b, model=_abi.MODEL_BVE_GYRE, grid=wl.nx,
+                   forcing_amp=1.0 / wl.ro, integrator=_abi.RK3_TVD)
 
     def close(self):
         if getattr(self, "h", None):

@@ -20,6 +20,7 @@ ERR_STATE = -8
 MODEL_BURGERS1D = 1
 MODEL_BVE2D = 2
 MODEL_BURGERS1D_DIRICHLET = 3
+MODEL_BVE_GYRE = 4
 RK4, RK3_TVD = 0, 1
 PRIOR_DIRICHLET_INV_HELMHOLTZ = 3
 FP64 = 0

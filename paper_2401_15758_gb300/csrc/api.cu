@@ -145,6 +145,7 @@ template <> const float* traj_of<float>(Prob* P) { return P->traj32; }
 
 static bool is_bve(const Prob* P) { return P->model == SC4DVAR_MODEL_BVE2D; }
 static bool is_dir(const Prob* P) { return P->model == SC4DVAR_MODEL_BURGERS1D_DIRICHLET; }
+static bool is_gyre(const Prob* P) { return P->model == SC4DVAR_MODEL_BVE_GYRE; }
 
 // Y = Gamma^{1/2} X (+ Z) for k columns: the 1D circulant (FFT), the 2D
 // spectral multiplier of the model's grid, or the tridiagonal inverse of the
@@ -153,6 +154,10 @@ template <typename TI, typename TO, typename TZ>
 static int prior_any(Prob* P, int k, const TI* X, int ldx, TO* Y, int ldy, const TZ* Z, int ldz,
                      cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
+  if (is_gyre(P)) {
+    SC4_TRY(P->wGyPrior.ensure(gyre_prior_ws_bytes(P->gy, k, sizeof(double))));
+    return gyre_prior_apply<TI, TO, TZ>(P->gy, k, X, ldx, Y, ldy, Z, ldz, P->wGyPrior.p, st);
+  }
   if (is_dir(P)) {
     SC4_TRY(P->wDir.ensure((size_t)P->n * k * sizeof(double)));
     P->dir.work = P->wDir.as<double>();
@@ -170,6 +175,10 @@ static int prior_any(Prob* P, int k, const TI* X, int ldx, TO* Y, int ldy, const
 template <typename T>
 static int model_tlm(Prob* P, const T* U, int ldu, int k, T* W, int ldw, cudaStream_t st) {
   if (is_dir(P)) return dir_tlm<T>(P->dir, traj_of<T>(P), U, ldu, k, W, ldw, st);
+  if (is_gyre(P)) {
+    SC4_TRY(P->wGy.ensure(gyre_sweep_ws_bytes(P->gy, k, sizeof(T))));
+    return gyre_tlm<T>(P->gy, U, ldu, k, W, ldw, P->wGy.p, st);
+  }
   if (!is_bve(P)) return burgers_tlm<T>(P->geom, traj_of<T>(P), U, ldu, k, W, ldw, st);
   SC4_TRY(P->wBve.ensure(bve_sweep_ws_bytes(P->bve, k, sizeof(T))));
   return bve_tlm<T>(P->bve, U, ldu, k, W, ldw, P->wBve.p, st);
@@ -179,6 +188,10 @@ static int model_tlm(Prob* P, const T* U, int ldu, int k, T* W, int ldw, cudaStr
 template <typename T>
 static int model_adj(Prob* P, const T* W, int ldw, int k, T* L, int ldl, cudaStream_t st) {
   if (is_dir(P)) return dir_adj<T>(P->dir, traj_of<T>(P), W, ldw, k, L, ldl, st);
+  if (is_gyre(P)) {
+    SC4_TRY(P->wGy.ensure(gyre_sweep_ws_bytes(P->gy, k, sizeof(T))));
+    return gyre_adj<T>(P->gy, W, ldw, k, L, ldl, P->wGy.p, st);
+  }
   if (!is_bve(P)) return burgers_adj<T>(P->geom, traj_of<T>(P), W, ldw, k, L, ldl, st);
   SC4_TRY(P->wBve.ensure(bve_sweep_ws_bytes(P->bve, k, sizeof(T))));
   return bve_adj<T>(P->bve, W, ldw, k, L, ldl, P->wBve.p, st);
@@ -282,12 +295,13 @@ static int hvp_vec_launch(Prob* P, const double* p, double* q, int prec, cudaStr
 // handle's private stream and replayed on the caller's stream. The first call
 // of a key runs eagerly (it sizes the work arrays, so nothing allocates during
 // recording); a recording is discarded when a work array has moved since.
-static void hvp_bufs(Prob* P, void* (&b)[5]) {
+static void hvp_bufs(Prob* P, void* (&b)[7]) {
   b[0] = P->wBve.p; b[1] = P->wCplx.p; b[2] = P->wU.p; b[3] = P->wW.p; b[4] = P->wL.p;
+  b[5] = P->wGy.p; b[6] = P->wGyPrior.p;
 }
 
 static int hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t st) {
-  if (!is_bve(P)) return hvp_vec_launch(P, p, q, prec, st);
+  if (!is_bve(P) && !is_gyre(P)) return hvp_vec_launch(P, p, q, prec, st);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
@@ -307,10 +321,10 @@ static int hvp_vec(Prob* P, const double* p, double* q, int prec, cudaStream_t s
     P->hvp_graphs.push_back(g);
     return SC4DVAR_OK;
   }
-  void* now[5];
+  void* now[7];
   hvp_bufs(P, now);
   bool same = true;
-  for (int i = 0; i < 5; ++i) same = same && now[i] == e->bufs[i];
+  for (int i = 0; i < 7; ++i) same = same && now[i] == e->bufs[i];
   if (e->exec && !same) {
     cudaGraphExecDestroy(e->exec);
     e->exec = nullptr;
@@ -933,6 +947,9 @@ static int fwd_run(Prob* P, const double* v, double* J_host, double* d_out, cuda
   SC4_TRY(prior_any<double, double, double>(P, 1, P->v, n, P->x0, n, P->xb, n, st));
   if (is_dir(P)) {
     SC4_TRY(dir_fwd(P->dir, P->x0, P->traj64, P->traj32, P->y, P->d, nullptr, nullptr, st));
+  } else if (is_gyre(P)) {
+    SC4_TRY(P->wGy.ensure(gyre_sweep_ws_bytes(P->gy, 1, 8)));
+    SC4_TRY(gyre_fwd(P->gy, P->x0, true, P->y, P->d, nullptr, nullptr, P->wGy.p, st));
   } else if (is_bve(P)) {
     SC4_TRY(P->wBve.ensure(std::max(bve_fwd_ws_bytes(P->bve), bve_sweep_ws_bytes(P->bve, 1, 8))));
     SC4_TRY(bve_fwd(P->bve, P->x0, true, P->y, P->d, nullptr, nullptr, P->wBve.p, st));
@@ -1030,13 +1047,23 @@ long long sc4dvar_launch_count(void) { return g_launches.load(); }
 int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out) {
   SC4_ARG(d && out, "null descriptor or output");
   SC4_ARG(d->model == SC4DVAR_MODEL_BURGERS1D || d->model == SC4DVAR_MODEL_BVE2D ||
-              d->model == SC4DVAR_MODEL_BURGERS1D_DIRICHLET,
+              d->model == SC4DVAR_MODEL_BURGERS1D_DIRICHLET || d->model == SC4DVAR_MODEL_BVE_GYRE,
           "unknown model");
   const bool bve = d->model == SC4DVAR_MODEL_BVE2D;
   const bool dirm = d->model == SC4DVAR_MODEL_BURGERS1D_DIRICHLET;
-  SC4_ARG(d->integrator == SC4DVAR_RK4 || (dirm && d->integrator == SC4DVAR_RK3_TVD),
-          "integrator: RK4, or RK3-TVD for the Dirichlet Burgers model");
-  if (dirm) {
+  const bool gym = d->model == SC4DVAR_MODEL_BVE_GYRE;
+  SC4_ARG(d->integrator == SC4DVAR_RK4 || ((dirm || gym) && d->integrator == SC4DVAR_RK3_TVD),
+          "integrator: RK4, or RK3-TVD for the Dirichlet Burgers and double-gyre models");
+  if (gym) {
+    SC4_ARG(d->nx >= 8 && d->nx <= 128 && (d->nx & (d->nx - 1)) == 0 && d->ny == 2 * d->nx + 1,
+            "double gyre: nx a power of two in [8, 128] and ny = 2 nx + 1");
+    SC4_ARG(d->prior_kind == SC4DVAR_PRIOR_DIRICHLET_INV_HELMHOLTZ && d->prior_sigma >= 0 &&
+                d->prior_length > 0,
+            "double-gyre prior: SC4DVAR_PRIOR_DIRICHLET_INV_HELMHOLTZ with a = prior_sigma >= 0, "
+            "b = prior_length > 0");
+    SC4_ARG(d->forcing_amp > 0, "double gyre: forcing_amp = 1/Ro must be positive");
+    SC4_ARG(d->n_checkpoints == 0, "checkpointing covers the doubly periodic BVE model (n_checkpoints must be 0)");
+  } else if (dirm) {
     SC4_ARG(d->nx >= 3 && d->nx <= 1024 && d->ny == 1, "Dirichlet Burgers: n interior points in [3, 1024]");
     SC4_ARG(d->prior_kind == SC4DVAR_PRIOR_DIRICHLET_INV_HELMHOLTZ && d->prior_sigma > 0 &&
                 d->prior_length >= 0,
@@ -1055,7 +1082,7 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
             "Burgers n must be a power of two in [8, 8192]");
     SC4_ARG(d->n_checkpoints == 0, "checkpointing covers the BVE model (n_checkpoints must be 0)");
   }
-  int n = bve ? d->nx * d->ny : d->nx;
+  int n = (bve || gym) ? d->nx * d->ny : d->nx;
   SC4_ARG(d->n_steps >= 1 && d->dt > 0 && d->nu >= 0, "time window");
   SC4_ARG(d->n_obs_times >= 1 && d->n_obs >= 1 && d->obs_steps && d->obs_idx, "observations");
   SC4_ARG(d->sigma_obs > 0, "sigma_obs must be positive");
@@ -1065,7 +1092,7 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   }
   for (long i = 0; i < (long)d->n_obs_times * d->n_obs; ++i)
     SC4_ARG(d->obs_idx[i] >= 0 && d->obs_idx[i] < n, "obs_idx out of range");
-  SC4_ARG(bve || dirm || d->prior_kind == SC4DVAR_PRIOR_SE ||
+  SC4_ARG(bve || dirm || gym || d->prior_kind == SC4DVAR_PRIOR_SE ||
               (d->prior_kind == SC4DVAR_PRIOR_SYMBOL && d->prior_symbol),
           "prior");
   SC4_ARG(d->prior_kind != SC4DVAR_PRIOR_SE || (d->prior_sigma > 0 && d->prior_length > 0),
@@ -1087,7 +1114,7 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   std::vector<int> oos(P->N + 1, -1);
   for (int i = 0; i < P->n_t; ++i) oos[d->obs_steps[i]] = i;
   P->obs_of_step_h = oos;
-  size_t traj_pts = bve ? 0 : (size_t)(P->N + 1) * n;
+  size_t traj_pts = (bve || gym) ? 0 : (size_t)(P->N + 1) * n;
   if (bve) {
     const int Ng = d->nx;
     // Checkpointing: L = ceil(N / c) steps per segment; the stage-state buffers
@@ -1123,16 +1150,16 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   }
   if (cudaMalloc(&P->obs_of_step, oos.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&P->obs_idx, (size_t)P->m * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&P->sym, (bve || dirm ? 1 : n) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&P->tw, (bve || dirm ? 1 : n / 2) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&P->sym, (bve || dirm || gym ? 1 : n) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&P->tw, (bve || dirm || gym ? 1 : n / 2) * sizeof(double2)) != cudaSuccess ||
       (dirm && cudaMalloc(&P->dir_cp, 2 * (size_t)n * sizeof(double)) != cudaSuccess) ||
       cudaMalloc(&P->xb, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->y, P->m * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->v, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->x0, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&P->d, P->m * sizeof(double)) != cudaSuccess ||
-      (!bve && cudaMalloc(&P->traj64, traj_pts * sizeof(double)) != cudaSuccess) ||
-      (!bve && cudaMalloc(&P->traj32, traj_pts * sizeof(float)) != cudaSuccess)) {
+      (traj_pts && cudaMalloc(&P->traj64, traj_pts * sizeof(double)) != cudaSuccess) ||
+      (traj_pts && cudaMalloc(&P->traj32, traj_pts * sizeof(float)) != cudaSuccess)) {
     cudaGetLastError();
     set_error("problem_create: device allocation failed");
     return fail(SC4DVAR_ERR_OOM);
@@ -1156,7 +1183,7 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
   P->geom.n_o = P->n_o;
   P->geom.obs_of_step = P->obs_of_step;
   P->geom.obs_idx = P->obs_idx;
-  P->geom.fold32 = (!bve && !dirm && packed_f32_supported(n)) ? 1 : 0;
+  P->geom.fold32 = (!bve && !dirm && !gym && packed_f32_supported(n)) ? 1 : 0;
   if (bve) {
     BveGeom& b = P->bve;
     b.N = d->nx;
@@ -1187,6 +1214,65 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
     b.ckpt = P->bve_ckpt;
     b.rws = P->bve_rws;
     if ((rc = bve_setup(b, 0))) return fail(rc);
+  } else if (gym) {
+    GyreGeom& g = P->gy;
+    g.nx = d->nx;
+    g.ny = d->ny;
+    g.n = n;
+    g.N = P->N;
+    g.n_t = P->n_t;
+    g.n_o = P->n_o;
+    g.dt = P->h;
+    g.h = 1.0 / (d->nx + 1);
+    g.re_inv = d->nu;
+    g.ro_inv = d->forcing_amp;
+    g.sigma = P->sigma;
+    for (int i = 0; i < 4; ++i) {
+      g.b[i] = 0.0;
+      for (int j = 0; j < 4; ++j) g.a[i][j] = 0.0;
+    }
+    if (d->integrator == SC4DVAR_RK3_TVD) {
+      g.S = 3;
+      g.a[1][0] = 1.0;
+      g.a[2][0] = 0.25;
+      g.a[2][1] = 0.25;
+      g.b[0] = 1.0 / 6.0;
+      g.b[1] = 1.0 / 6.0;
+      g.b[2] = 2.0 / 3.0;
+    } else {
+      g.S = 4;
+      g.a[1][0] = 0.5;
+      g.a[2][1] = 0.5;
+      g.a[3][2] = 1.0;
+      g.b[0] = g.b[3] = 1.0 / 6.0;
+      g.b[1] = g.b[2] = 1.0 / 3.0;
+    }
+    g.obs_of_step = P->obs_of_step;
+    g.obs_of_step_h = P->obs_of_step_h.data();
+    g.obs_idx = P->obs_idx;
+    const size_t nn = (size_t)g.nx * g.nx, f = 2 * (size_t)g.nx * g.ny;
+    const size_t st_pts = (size_t)g.N * g.S * n;
+    if (cudaMalloc(&P->gy_setup, gyre_setup_bytes(g.nx)) != cudaSuccess ||
+        cudaMalloc(&P->gy_stages, gyre_stage_bytes(g.nx, g.N, g.S)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("problem_create: device allocation of the double-gyre arrays failed");
+      return fail(SC4DVAR_ERR_OOM);
+    }
+    char* b = static_cast<char*>(P->gy_setup);
+    g.S64 = reinterpret_cast<double*>(b);
+    g.pois64 = reinterpret_cast<double*>(b + nn * 8);
+    g.prior64 = reinterpret_cast<double*>(b + nn * 8 + f * 8);
+    g.Fy = reinterpret_cast<double*>(b + nn * 8 + 2 * f * 8);
+    char* b4 = b + nn * 8 + 2 * f * 8 + (size_t)g.ny * 8;
+    g.S32 = reinterpret_cast<float*>(b4);
+    g.pois32 = reinterpret_cast<float*>(b4 + nn * 4);
+    g.prior32 = reinterpret_cast<float*>(b4 + nn * 4 + f * 4);
+    char* sb = static_cast<char*>(P->gy_stages);
+    g.om64 = reinterpret_cast<double*>(sb);
+    g.ps64 = reinterpret_cast<double*>(sb + st_pts * 8);
+    g.om32 = reinterpret_cast<float*>(sb + 2 * st_pts * 8);
+    g.ps32 = reinterpret_cast<float*>(sb + 2 * st_pts * 8 + st_pts * 4);
+    if ((rc = gyre_setup(g, d->prior_sigma, d->prior_length, 0))) return fail(rc);
   } else if ((rc = fft_make_twiddles(n, P->tw, 0))) {
     return fail(rc);
   }
@@ -1225,8 +1311,8 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
     g.work = nullptr;
     g.work_cols = 0;
     if ((rc = dir_setup(g, d->prior_sigma, d->prior_length, 0))) return fail(rc);
-  } else if (bve) {
-    // prior handled by the 2D multiplier
+  } else if (bve || gym) {
+    // prior handled by the 2D multiplier / the sine-transform solve
   } else if (d->prior_kind == SC4DVAR_PRIOR_SE) {
     if ((rc = fft_se_symbol(n, d->prior_sigma, d->prior_length, kClampRel, P->tw, P->sym, 0)))
       return fail(rc);
@@ -1251,6 +1337,10 @@ int sc4dvar_problem_destroy(sc4dvar_problem_t P) {
   cudaFree(P->traj64); cudaFree(P->traj32); cudaFree(P->dir_cp); cudaFree(P->traj_df);
   P->wDF.release();
   P->wDir.release();
+  cudaFree(P->gy_setup);
+  cudaFree(P->gy_stages);
+  P->wGy.release();
+  P->wGyPrior.release();
   cudaFree(P->bve_tw64); cudaFree(P->bve_tw32); cudaFree(P->bve_poisson); cudaFree(P->bve_prior);
   cudaFree(P->bve_tabc64); cudaFree(P->bve_tabc32);
   cudaFree(P->bve_q64); cudaFree(P->bve_p64); cudaFree(P->bve_q32); cudaFree(P->bve_p32);
@@ -1294,7 +1384,7 @@ int sc4dvar_prior_sqrt_apply(sc4dvar_problem_t P, const double* X, int ldx, int 
 
 int sc4dvar_prior_symbol(sc4dvar_problem_t P, double* symbol_host) {
   SC4_ARG(P && symbol_host, "null argument");
-  SC4_ARG(!is_dir(P), "the Dirichlet prior has no Fourier symbol");
+  SC4_ARG(!is_dir(P) && !is_gyre(P), "the Dirichlet prior has no Fourier symbol");
   if (is_bve(P)) {
     SC4_CUDA(cudaMemcpy(symbol_host, P->bve.prior, P->n * sizeof(double), cudaMemcpyDeviceToHost));
     return SC4DVAR_OK;
@@ -1306,6 +1396,10 @@ int sc4dvar_prior_symbol(sc4dvar_problem_t P, double* symbol_host) {
 int sc4dvar_forecast(sc4dvar_problem_t P, const double* x0, double* obs, double* xN, void* stream) {
   SC4_ARG(P && x0 && obs, "null argument");
   if (is_dir(P)) return dir_fwd(P->dir, x0, nullptr, nullptr, nullptr, nullptr, obs, xN, S(stream));
+  if (is_gyre(P)) {
+    SC4_TRY(P->wGy.ensure(gyre_sweep_ws_bytes(P->gy, 1, 8)));
+    return gyre_fwd(P->gy, x0, false, nullptr, nullptr, obs, xN, P->wGy.p, S(stream));
+  }
   if (is_bve(P)) {
     SC4_TRY(P->wBve.ensure(std::max(bve_fwd_ws_bytes(P->bve), P->wBve.bytes)));
     return bve_fwd(P->bve, x0, false, nullptr, nullptr, obs, xN, P->wBve.p, S(stream));

@@ -463,7 +463,14 @@ int cluster_for(int H, int k, int arrays) {
   int cl = 1;
   while ((size_t)(arrays * (H / cl + 2 * kPad2) + 256) * sizeof(f2) > kMaxSmem2 && cl < 16) cl *= 2;
   if (k <= 4) {
-    while (cl < 8 && H / (cl * 2) >= 256) cl *= 2;
+    // few directions: spread each over up to 8 CTAs; SC4DVAR_FEW_CLUSTER caps
+    // the spread (a tuning knob: 1, 2, 4 or 8)
+    static int cap = [] {
+      const char* e = getenv("SC4DVAR_FEW_CLUSTER");
+      int c = e ? atoi(e) : 8;
+      return (c == 1 || c == 2 || c == 4) ? c : 8;
+    }();
+    while (cl < cap && H / (cl * 2) >= 256) cl *= 2;
   }
   return cl;
 }

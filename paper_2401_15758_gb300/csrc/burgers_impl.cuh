@@ -392,7 +392,11 @@ static int pick_P_v2(int seg, size_t tb) {
     const char* e = getenv("SC4DVAR_SWEEP_P");
     return e ? atoi(e) : 0;
   }();
-  int want = tb == 4 ? (forced > 0 ? std::min(forced, 32) : 16) : 4;
+  static int forced8 = [] {
+    const char* e = getenv("SC4DVAR_SWEEP_P8");
+    return e ? atoi(e) : 0;
+  }();
+  int want = tb == 4 ? (forced > 0 ? std::min(forced, 32) : 16) : (forced8 > 0 ? std::min(forced8, 4) : 4);
   int P = 1;
   while (P < want && seg / (2 * P) >= 256) P *= 2;
   while (seg / P > threads_bound(P, tb) && P < max_P_v2(tb)) P *= 2;
@@ -409,8 +413,15 @@ static int pick_cluster(int n, int k, size_t tb, int kind) {
     cl *= 2;
   if (k <= 4) {
     // few directions: spread each over up to 16 CTAs (non-portable cluster size)
-    // while a CTA keeps at least 512 points
-    while (cl < 16 && n / (cl * 2) >= 512) cl *= 2;
+    // while a CTA keeps at least 512 points; SC4DVAR_FEW_CLUSTER8 caps the
+    // spread for 8-byte types (a tuning knob: 1, 2, 4, 8 or 16)
+    static int cap8 = [] {
+      const char* e = getenv("SC4DVAR_FEW_CLUSTER8");
+      int c = e ? atoi(e) : 16;
+      return (c == 1 || c == 2 || c == 4 || c == 8) ? c : 16;
+    }();
+    const int cap = tb == 8 ? cap8 : 16;
+    while (cl < cap && n / (cl * 2) >= 512) cl *= 2;
   }
   return cl;
 }

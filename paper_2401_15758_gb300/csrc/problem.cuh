@@ -6,6 +6,7 @@
 #include "model.cuh"
 #include "bve.cuh"
 #include "dirichlet.cuh"
+#include "gyre.cuh"
 #include <vector>
 
 namespace sc4 {
@@ -69,6 +70,11 @@ struct sc4dvar_problem_s {
   sc4::DirGeom dir{};
   double* dir_cp = nullptr;
   sc4::Buf wDir;
+  // double-gyre vorticity problems: geometry, set-up arrays, stage states, work
+  sc4::GyreGeom gy{};
+  void* gy_setup = nullptr;
+  void* gy_stages = nullptr;
+  sc4::Buf wGy, wGyPrior;
   double* bve_ckpt = nullptr;  // checkpoint states (checkpointing only)
   void* bve_rws = nullptr;     // segment recompute workspace (checkpointing only)
   sc4::Buf wBve, wCplx;
@@ -82,7 +88,7 @@ struct sc4dvar_problem_s {
     const double* p;
     double* q;
     int prec;
-    void* bufs[5];
+    void* bufs[7];
     cudaGraphExec_t exec;
     bool eager_only;
   };
