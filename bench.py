@@ -59,8 +59,11 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-gn-step", action="store_true", help="skip the time-to-solution part")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256", "bve_n1024", "burgers_batch64", "burgers_paper"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256", "bve_n1024", "burgers_batch64", "burgers_paper",
+                                                             "bve_gyre"],
                     help="the Burgers block (default) or the barotropic vorticity block")
+    ap.add_argument("--gn-iters", type=int, default=25,
+                    help="GN iterations of the double-gyre experiment (the paper runs 25)")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
     return ap.parse_args()
@@ -380,6 +383,47 @@ def batch_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def paper_counts(table):
+    """PDE-solve counts the paper prints for one table (tests/golden/paper_counts.txt)."""
+    paper = {}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_counts.txt")) as f:
+        for line in f:
+            if line.startswith(table + " "):
+                _, meth, *vals = line.split()
+                paper[meth] = [None if v == "-" else int(v) for v in vals]
+    return paper
+
+
+def paper_runs(torch, dev, problem, n, table, runs, iters, tol):
+    """Gauss-Newton from v = 0 for each (name, options) run on a fresh problem,
+    strong-Wolfe steps; PDE-solve counters and wall time next to the paper's
+    counts of the same method."""
+    paper = paper_counts(table)
+    rows = {}
+    for name, opts in runs:
+        p = problem()
+        p.counters_reset()
+        v = torch.zeros(n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rec = p.gauss_newton(v, iters=iters, tol=tol, gtol=1e-6, line_search=True, **opts)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        c = p.counters()
+        ours = {"pcg_its": sum(r["pcg_its"] for r in rec), "tlm_off": c["tlm_offline"],
+                "adj_off": c["adj_offline"], "fwd": c["fwd"], "tlm_on": c["tlm_online"],
+                "adj_on": c["adj_online"], "gn_iters": len(rec), "J_final": rec[-1]["J"],
+                "sketched_at": [i + 1 for i, r in enumerate(rec) if r["sketched"]],
+                "ranks": sorted({r["rank"] for r in rec}),
+                "alphas": [r["alpha"] for r in rec], "seconds": secs}
+        pr = paper.get(name)
+        rows[name] = {"ours": ours, "paper": None if pr is None else dict(
+            zip(("pcg_its", "tlm_off", "adj_off", "fwd", "tlm_on", "adj_on"), pr))}
+        print(f"{name}: {json.dumps(ours)}", file=sys.stderr, flush=True)
+        p.close()
+    return rows
+
+
 def paper_arm(args):
     """The Burgers experiment of Sec. 5.1 (Dirichlet, RK3-TVD, n = 399, 8000 steps,
     15 sites, 20 times): 3 GN iterations with l = l1 = 15, l2 = 31, PCG to 1e-9,
@@ -402,37 +446,13 @@ def paper_arm(args):
         p.set_background(xt + p.prior_sqrt_apply(torch.tensor(d["xi_b"], device=dev)))
         return p
 
-    paper = {}
-    gold = os.path.join(ROOT, "tests", "golden", "paper_counts.txt")
-    with open(gold) as f:
-        for line in f:
-            if line.startswith("T3 "):
-                t, meth, *vals = line.split()
-                paper[meth] = [None if v == "-" else int(v) for v in vals]
-    runs = [("none", "pcg", "Prec_Gamma"), ("randsvd", "pcg", "SketchPrec_RandSVD"),
-            ("nystrom", "pcg", "SketchPrec_Nystrom"), ("singleview", "pcg", "SketchPrec_SingleView"),
-            ("randsvd", "sketchsolv", "SketchSolv_RandSVD"), ("nystrom", "sketchsolv", "SketchSolv_Nystrom"),
-            ("singleview", "sketchsolv", "SketchSolv_SingleView")]
-    rows = {}
-    for method, solve, name in runs:
-        p = problem()
-        p.counters_reset()
-        v = torch.zeros(wl.n, dtype=torch.float64, device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rec = p.gauss_newton(v, iters=3, method=method, l=wl.k, l2=2 * wl.k + 1, tol=1e-9, gtol=1e-6,
-                             line_search=True, solve=solve)
-        torch.cuda.synchronize()
-        secs = time.perf_counter() - t0
-        c = p.counters()
-        ours = {"pcg_its": sum(r["pcg_its"] for r in rec), "tlm_off": c["tlm_offline"],
-                "adj_off": c["adj_offline"], "fwd": c["fwd"], "tlm_on": c["tlm_online"],
-                "adj_on": c["adj_online"], "gn_iters": len(rec), "J_final": rec[-1]["J"],
-                "alphas": [r["alpha"] for r in rec], "seconds": secs}
-        pr = paper.get(name)
-        rows[name] = {"ours": ours, "paper": None if pr is None else dict(
-            zip(("pcg_its", "tlm_off", "adj_off", "fwd", "tlm_on", "adj_on"), pr))}
-        p.close()
+    runs = [(name, dict(method=method, solve=solve, l=wl.k, l2=2 * wl.k + 1))
+            for method, solve, name in
+            [("none", "pcg", "Prec_Gamma"), ("randsvd", "pcg", "SketchPrec_RandSVD"),
+             ("nystrom", "pcg", "SketchPrec_Nystrom"), ("singleview", "pcg", "SketchPrec_SingleView"),
+             ("randsvd", "sketchsolv", "SketchSolv_RandSVD"), ("nystrom", "sketchsolv", "SketchSolv_Nystrom"),
+             ("singleview", "sketchsolv", "SketchSolv_SingleView")]]
+    rows = paper_runs(torch, dev, problem, wl.n, "T3", runs, iters=3, tol=1e-9)
     # timed step: FP64 block product of the sketch size
     p = problem()
     p.fwd(torch.zeros(wl.n, dtype=torch.float64, device=dev))
@@ -457,6 +477,98 @@ def paper_arm(args):
                                   f"{wl.n_steps} steps, m={wl.m}, block k={wl.k}, FP64",
                       "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": wl.k},
            "paper_table3_comparison": rows}
+    print(json.dumps(out), flush=True)
+
+
+def gyre_arm(args):
+    """The barotropic vorticity experiment of Sec. 5.2 (double gyre in a closed
+    basin, 128 x 257 interior points, RK3-TVD, 40 steps, 8 observation times of
+    a 16 x 16 sensor grid): 25 GN iterations, PCG to 1e-9, strong-Wolfe steps,
+    FP64, for Prec_Gamma, the three sketches with l = l1 = 384 (l2 = 769)
+    recomputed every iteration (SketchPrec), and the adaptive sketches with the
+    reuse rule (SketchPrecA: l0 = l_hat = 128, eps_sk = 1.01, eps_re = 10);
+    PDE-solve counts and times next to the counts the paper prints (Table 4).
+    The timed step is the FP64 block product of the sketch size (k = 384)."""
+    import torch
+    import paper_2401_15758_gb300 as g
+    import sc4dvar_inputs as si
+    dev = torch.device("cuda", 0)
+    wl = si.gyre_workload()
+    d = si.gyre_draws(wl)
+    # spun-up truth: init_scale Gamma^{1/2} xi_init advanced spin_steps steps by
+    # the library's own forecast over a window of that length
+    spin = si.gyre_workload(obs_every=wl.spin_steps // 8, n_obs_times=8)
+    ps = g.Problem.from_gyre_workload(spin, si.gyre_draws(spin))
+    x_init = wl.init_scale * ps.prior_sqrt_apply(torch.tensor(d["xi_init"], device=dev))
+    _, xt = ps.forecast(x_init)
+    ps.close()
+
+    def problem():
+        p = g.Problem.from_gyre_workload(wl, d)
+        obs, _ = p.forecast(xt)
+        p.set_observations(obs + wl.sigma_obs * torch.tensor(d["xi_o"].reshape(-1), device=dev))
+        p.set_background(xt + p.prior_sqrt_apply(torch.tensor(d["xi_b"], device=dev)))
+        return p
+
+    fixed = dict(l=wl.k, l2=2 * wl.k + 1)
+    adapt = dict(adaptive=True, l=128, l_hat=128, l2=257, l_max=2048, eps_sk=1.01, eps_re=10.0)
+    runs = [("Prec_Gamma", dict(method="none")),
+            ("SketchPrec_RandSVD", dict(method="randsvd", **fixed)),
+            ("SketchPrec_Nystrom", dict(method="nystrom", **fixed)),
+            ("SketchPrec_SingleView", dict(method="singleview", **fixed)),
+            ("SketchPrecA_RandSVD", dict(method="randsvd", **adapt)),
+            ("SketchPrecA_Nystrom", dict(method="nystrom", **adapt)),
+            ("SketchPrecA_SingleView", dict(method="singleview", **adapt))]
+    if args.gn_iters < 25:
+        runs = [r for r in runs if r[0] != "Prec_Gamma"] + [("Prec_Gamma", dict(method="none"))]
+    p = problem()
+    p.fwd(torch.zeros(wl.n, dtype=torch.float64, device=dev))
+    X = torch.tensor(si.gaussian_matrix(wl.seed, wl.k, wl.n, stream=29), device=dev)
+    X32 = X.float()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(e))
+        return statistics.mean(ms) / 1e3
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = g.lib.sc4dvar_launch_count()
+    t = timed(lambda: p.gn_hessian_apply_block(X))
+    launches = (g.lib.sc4dvar_launch_count() - l0) // (args.warmup + args.steps)
+    t32 = timed(lambda: p.gn_hessian_apply_block(X32, prec=g.FP32))
+    clk = clocks.stop()
+    x1 = X[:1].contiguous()
+    t1 = timed(lambda: p.gn_hessian_apply_block(x1))
+    p.close()
+    print(f"block k={wl.k}: FP64 {1e3 * t:.2f} ms, FP32 {1e3 * t32:.2f} ms; one FP64 product {1e3 * t1:.3f} ms",
+          file=sys.stderr, flush=True)
+    rows = paper_runs(torch, dev, problem, wl.n, "T4", runs, iters=args.gn_iters, tol=wl.pcg_tol)
+    out = {"metric": METRIC, "value": wl.k / t, "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{wl.name}: double-gyre vorticity {wl.nx}x{wl.ny} (Dirichlet), "
+                                  f"Re={wl.re}, Ro={wl.ro}, RK3-TVD, {wl.n_steps} steps, m={wl.m}, "
+                                  f"block k={wl.k}, FP64",
+                      "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": wl.k, "gn_iters": args.gn_iters,
+                      "l2": "256 MiB write before every timed step"},
+           "fp32_block": {"value": wl.k / t32, "unit": "HVP/s", "ms_per_step": 1e3 * t32},
+           "single_fp64_product_ms": 1e3 * t1,
+           "gpu_launches_per_step": int(launches), "clocks": clk,
+           "paper_table4_comparison": rows}
     print(json.dumps(out), flush=True)
 
 
@@ -693,6 +805,8 @@ def main():
         batch_arm(args)
     elif args.workload == "burgers_paper":
         paper_arm(args)
+    elif args.workload == "bve_gyre":
+        gyre_arm(args)
     else:
         gpu_arm(args)
 

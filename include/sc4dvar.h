@@ -329,6 +329,20 @@ int sc4dvar_pcg(sc4dvar_problem_t p, sc4dvar_precond_t P, const double* b_dev, d
 /* SketchSolv step (Eq. dxsol, in v): dv = -(I + H_hat)^{-1} g. */
 int sc4dvar_sketchsolv(sc4dvar_precond_t P, const double* g_dev, double* dv_dev, void* stream);
 
+/* QR update of Alg. 6 (used by the adaptive SingleView sketch of Alg. 5 for the
+ * QR of M = Psi^T Q_Y as Psi and Q_Y gain columns). All FP64, device,
+ * column-major, caller-owned. A1 = P[:, 0:r1]^T and A2 = P[:, r1:r1+r2]^T, with
+ * P m x (r1 + r2) (ld ldp); B1 = B[:, 0:k1] and B2 = B[:, k1:k1+k2] (ld ldb),
+ * whose columns are orthonormal. On entry Q[0:r1, 0:k1] (ld ldq) and
+ * R[0:k1, 0:k1] (ld ldr, upper triangular) hold Q1 R1 = A1 B1; on return
+ * Q[0:r1+r2, 0:k1+k2] and R[0:k1+k2, 0:k1+k2] (upper triangular, zeros below the
+ * diagonal) hold the thin QR of [A1; A2] [B1 B2]. Needs r1 >= k1 and
+ * r1 + r2 >= k1 + k2, else ERR_INVALID_ARG; ERR_NOT_SPD if a block is rank
+ * deficient. Allocates its workspace; synchronizes. */
+int sc4dvar_qr_update(int m, int r1, int r2, int k1, int k2, const double* P_dev, int ldp,
+                      const double* B_dev, int ldb, double* Q_dev, int ldq, double* R_dev, int ldr,
+                      void* stream);
+
 /* Gauss-Newton from v_inout (overwritten with the final iterate): per iteration
  * FWD, gradient, sketch (every iteration when fixed; when adaptive, the last
  * sketch is reused while kappa_re < eps_re, Sec. 3.2), PCG, v += alpha dv with

@@ -425,3 +425,23 @@ def gaussian(seed, stream_id, rows, cols, col0=0, stream=None):
     out = torch.empty((cols, rows), dtype=torch.float64, device="cuda")
     check(lib.sc4dvar_gaussian(seed, stream_id, rows, cols, col0, _ptr(out), _stream(stream)))
     return out
+
+
+def qr_update(P, B, Q1, R1, r1, k1, stream=None):
+    """Alg. 6: the thin QR of [A1; A2][B1 B2] from Q1 R1 = A1 B1, with
+    A1 = P[:, :r1]^T, A2 = P[:, r1:]^T, B1 = B[:, :k1], B2 = B[:, k1:].
+    P (m, r1 + r2) and B (m, k1 + k2) are float64 CUDA matrices in the usual
+    (row, column) shape; returns Q (r1 + r2, k1 + k2) and R (k1 + k2, k1 + k2)."""
+    torch = _torch()
+    m, ra = P.shape
+    kb = B.shape[1]
+    r2, k2 = ra - r1, kb - k1
+    Pc = P.t().contiguous()          # column-major m x ra
+    Bc = B.t().contiguous()
+    Qc = torch.zeros((kb, ra), dtype=torch.float64, device=P.device)   # column-major ra x kb
+    Rc = torch.zeros((kb, kb), dtype=torch.float64, device=P.device)
+    Qc[:k1, :r1] = Q1.t()
+    Rc[:k1, :k1] = R1.t()
+    check(lib.sc4dvar_qr_update(m, r1, r2, k1, k2, _ptr(Pc), m, _ptr(Bc), m, _ptr(Qc), ra,
+                                _ptr(Rc), kb, _stream(stream)))
+    return Qc.t(), Rc.t()

@@ -124,6 +124,7 @@ SIGNATURES = {
     "sc4dvar_kappa_estimate": (I, [P, P, U64, U64, I, C.POINTER(D), P]),
     "sc4dvar_pcg": (I, [P, P, P, P, C.POINTER(PcgOpts), C.POINTER(PcgInfo), P]),
     "sc4dvar_sketchsolv": (I, [P, P, P, P]),
+    "sc4dvar_qr_update": (I, [I, I, I, I, I, P, I, P, I, P, I, P, I, P]),
     "sc4dvar_gauss_newton": (I, [P, C.POINTER(GnOpts), P, C.POINTER(GnInfo), P]),
     "sc4dvar_counters": (I, [P, C.POINTER(Counters)]),
     "sc4dvar_counters_reset": (I, [P]),

@@ -83,6 +83,23 @@ __global__ void symmetrize_kernel(int l, double* A, int lda, double shift) {
   }
 }
 
+// A[:r, :c] = 0 (ld lda)
+__global__ void zero_block_kernel(int r, int c, double* A, int lda) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx < (size_t)r * c) A[(idx / r) * lda + idx % r] = 0.0;
+}
+
+// B = the upper triangle of A (zeros below the diagonal), or its transpose
+// (a lower triangle) when trans; l x l
+__global__ void triu_copy_kernel(int l, const double* A, int lda, double* B, int ldb, int trans) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < l * l) {
+    int i = idx % l, j = idx / l;
+    if (trans) B[(size_t)j * ldb + i] = (i >= j) ? A[(size_t)i * lda + j] : 0.0;
+    else B[(size_t)j * ldb + i] = (i <= j) ? A[(size_t)j * lda + i] : 0.0;
+  }
+}
+
 // B (l x r) = U[:, :r] * diag(1/sqrt(w)), and lam = max(0, w - nu) (first r)
 __global__ void svd_scale_kernel(int l, int r, const double* U, int ldu, const double* w,
                                  double nu, double* B, double* lam, double* dsc) {
@@ -728,31 +745,102 @@ static int build_nystrom(Prob* P, const sc4dvar_sketch_opts& o, const double* Om
   return rc;
 }
 
-// Alg. 3 / Alg. 5. W = R_M^dagger (Z Q_M)^T is formed as W^T = Z M (M^T M)^{-1}
-// (= Z Q_M R_M^{-T} for M = Psi^T Q_Y = Q_M R_M of full column rank).
+// Thin QR of an FP64 matrix A (rows x c, rows >= c): Q by CholeskyQR2, then
+// R = Q^T A with its lower triangle set to zero.
+static int qr_f64(int rows, int c, const double* A, int lda, double* Q, int ldq, double* R, int ldr,
+                  cudaStream_t st) {
+  if (c == 0) return SC4DVAR_OK;
+  SketchWS w;
+  Buf rt;
+  auto body = [&]() -> int {
+    SC4_TRY(cholqr2<double>(rows, c, A, lda, Q, ldq, w, st));
+    SC4_TRY(rt.ensure((size_t)c * c * sizeof(double)));
+    SC4_TRY(gemm_tn<double, double>(rows, c, c, 1.0, Q, ldq, A, lda, 0.0, rt.as<double>(), c, st));
+    triu_copy_kernel<<<div_up(c * c, 256), 256, 0, st>>>(c, rt.as<double>(), c, R, ldr, 0);
+    SC4_LAUNCH_CHECK();
+    return SC4DVAR_OK;
+  };
+  int rc = body();
+  cudaStreamSynchronize(st);
+  w.release();
+  rt.release();
+  return rc;
+}
+
+// Alg. 6 (QR update for adaptive SingleView). With A1 = P[:, :r1]^T,
+// A2 = P[:, r1:r1+r2]^T (P is m x (r1 + r2), ld ldp) and B1 = B[:, :k1],
+// B2 = B[:, k1:k1+k2] (orthonormal columns, ld ldb): on entry the leading
+// r1 x k1 block of Qm and k1 x k1 block of Rm hold Q1 R1 = A1 B1; on exit
+// Qm ((r1 + r2) x (k1 + k2)) and Rm ((k1 + k2) x (k1 + k2), upper triangular)
+// hold the thin QR of [A1; A2][B1 B2]. Steps 1-3 are taken together as the QR
+// of [R1; A2 B1] followed by blockdiag(Q1, I): when A2 B1 = Q2 R2,
+// [R1; A2 B1] = blockdiag(I, Q2) [R1; R2], so this is the QR of step 2 carried
+// through step 3, without the thin QR of A2 B1 (a wide r2 x k1 matrix once the
+// sketch has grown past r2 columns).
 template <typename T>
-static int singleview_W(Prob* P, int l1, int l2, const T* Psi, const T* QY, const T* Z, T* wt,
-                        SketchWS& ws, cudaStream_t st) {
-  const int n = P->n, m = P->m;
-  SC4_TRY(ws.b.ensure((size_t)l2 * l1 * sizeof(double)));
+static int qr_update(int m, int r1, int r2, int k1, int k2, const T* P, int ldp, const T* B, int ldb,
+                     double* Qm, int ldq, double* Rm, int ldr, cudaStream_t st) {
+  const int ra = r1 + r2, rs = k1 + r2;
+  Buf bS, bQ3s, bQ3, bP1;
+  auto body = [&]() -> int {
+    SC4_TRY(bS.ensure((size_t)rs * std::max(k1, 1) * sizeof(double)));
+    SC4_TRY(bQ3s.ensure((size_t)rs * std::max(k1, 1) * sizeof(double)));
+    SC4_TRY(bQ3.ensure((size_t)ra * std::max(k1, 1) * sizeof(double)));
+    SC4_TRY(bP1.ensure((size_t)ra * std::max(k2, 1) * sizeof(double)));
+    double *S = bS.as<double>(), *Q3s = bQ3s.as<double>(), *Q3 = bQ3.as<double>(), *P1 = bP1.as<double>();
+    if (k1 > 0) {
+      // steps 1-2: S = [R1; A2 B1], S = Q3s R3 (R3 into Rm's leading block)
+      SC4_TRY(copy_block<double, double>(k1, k1, Rm, ldr, S, rs, st));
+      SC4_TRY(gemm_tn<T, T>(m, r2, k1, 1.0, P + (size_t)ldp * r1, ldp, B, ldb, 0.0, S + k1, rs, st));
+      SC4_TRY(qr_f64(rs, k1, S, rs, Q3s, rs, Rm, ldr, st));
+      // step 3: Q3 = blockdiag(Q1, I) Q3s
+      SC4_TRY(gemm_nn<double, double>(r1, k1, k1, 1.0, Qm, ldq, Q3s, rs, 0, 0.0, Q3, ra, st));
+      SC4_TRY(copy_block<double, double>(r2, k1, Q3s + k1, rs, Q3 + r1, ra, st));
+    }
+    if (k2 > 0) {
+      // step 4: P1 = [A1; A2] B2
+      SC4_TRY(gemm_tn<T, T>(m, ra, k2, 1.0, P, ldp, B + (size_t)ldb * k1, ldb, 0.0, P1, ra, st));
+      if (k1 > 0) {
+        // step 5: Q3^T P1 (the upper-right block of R5), P2 = P1 - Q3 (Q3^T P1)
+        double* Rtr = Rm + (size_t)ldr * k1;
+        SC4_TRY(gemm_tn<double, double>(ra, k1, k2, 1.0, Q3, ra, P1, ra, 0.0, Rtr, ldr, st));
+        SC4_TRY(gemm_nn<double, double>(ra, k1, k2, -1.0, Q3, ra, Rtr, ldr, 0, 1.0, P1, ra, st));
+      }
+      // step 6: P2 = Q4 R4 into the new columns of Qm and the lower-right block of Rm
+      SC4_TRY(qr_f64(ra, k2, P1, ra, Qm + (size_t)ldq * k1, ldq, Rm + (size_t)ldr * k1 + k1, ldr, st));
+    }
+    if (k1 > 0) {
+      // step 7: Q5 = [Q3 Q4], R5 = [R3 Q3^T P1; 0 R4]
+      SC4_TRY(copy_block<double, double>(ra, k1, Q3, ra, Qm, ldq, st));
+      if (k2 > 0) {
+        zero_block_kernel<<<div_up(k2 * k1, 256), 256, 0, st>>>(k2, k1, Rm + k1, ldr);
+        SC4_LAUNCH_CHECK();
+      }
+    }
+    return SC4DVAR_OK;
+  };
+  int rc = body();
+  cudaStreamSynchronize(st);
+  bS.release(); bQ3s.release(); bQ3.release(); bP1.release();
+  return rc;
+}
+
+// Alg. 3 / Alg. 5: W = R_M^dagger (Z Q_M)^T with M = Psi^T Q_Y = Q_M R_M, formed
+// as W^T = Z (Q_M R_M^{-T}) (full column rank: R_M^dagger = R_M^{-1}).
+template <typename T>
+static int singleview_W(Prob* P, int l1, int l2, const double* Qm, int ldq, const double* Rm, int ldr,
+                        const T* Z, T* wt, SketchWS& ws, cudaStream_t st) {
+  const int n = P->n;
   SC4_TRY(ws.g.ensure((size_t)l1 * l1 * sizeof(double)));
   SC4_TRY(ws.g2.ensure((size_t)l1 * l1 * sizeof(double)));
   SC4_TRY(ws.u.ensure((size_t)l2 * l1 * sizeof(double)));
-  SC4_TRY(ws.info.ensure(64));
-  double* M = ws.b.as<double>();
-  double* G = ws.g.as<double>();
+  double* Lt = ws.g.as<double>();
   double* Li = ws.g2.as<double>();
   double* Bm = ws.u.as<double>();
-  SC4_TRY(gemm_tn<T, T>(m, l2, l1, 1.0, Psi, m, QY, m, 0.0, M, l2, st));       // M = Psi^T Q_Y
-  SC4_TRY(gemm_tn<double, double>(l2, l1, l1, 1.0, M, l2, M, l2, 0.0, G, l1, st));  // M^T M
-  SC4_TRY(chol_lower(l1, G, l1, ws.info.as<int>(), st));
-  SC4_TRY(check_info(ws.info, "SingleView M^T M", st));
-  SC4_TRY(trtri_lower(l1, G, l1, Li, l1, 0.0, st));
-  // Bm = M L^{-T} L^{-1}  (l2 x l1)
-  SC4_TRY(ws.w.ensure((size_t)l2 * l1 * sizeof(double)));
-  double* tmpm = ws.w.as<double>();
-  SC4_TRY(gemm_nn<double, double>(l2, l1, l1, 1.0, M, l2, Li, l1, 1, 0.0, tmpm, l2, st));
-  SC4_TRY(gemm_nn<double, double>(l2, l1, l1, 1.0, tmpm, l2, Li, l1, 0, 0.0, Bm, l2, st));
+  triu_copy_kernel<<<div_up(l1 * l1, 256), 256, 0, st>>>(l1, Rm, ldr, Lt, l1, 1);  // R_M^T
+  SC4_LAUNCH_CHECK();
+  SC4_TRY(trtri_lower(l1, Lt, l1, Li, l1, 0.0, st));                                 // R_M^{-T}
+  SC4_TRY(gemm_nn<double, double>(l2, l1, l1, 1.0, Qm, ldq, Li, l1, 0, 0.0, Bm, l2, st));
   // W^T = Z Bm  (n x l1)
   SC4_TRY(gemm_nn<T, T>(n, l2, l1, 1.0, Z, n, Bm, l2, 0, 0.0, wt, n, st));
   return SC4DVAR_OK;
@@ -773,8 +861,15 @@ static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double*
   const uint64_t s_ps = s_om + SC4DVAR_STREAM_PSI;
   const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
   SketchWS ws;
-  Buf Om, Ps, Y, QY, Z, Wt, tmp;
+  Buf Om, Ps, Y, QY, Z, Wt, tmp, Mq, Mr, Mb;
+  const int ldq = l2max, ldr = lmax;  // Q_M (l2 x l1) and R_M (l1 x l1) at their largest
   auto body = [&]() -> int {
+    SC4_ARG(l2_0 >= l1_0, "SingleView needs l2 >= l1");
+    SC4_TRY(Mq.ensure((size_t)ldq * lmax * sizeof(double)));
+    SC4_TRY(Mr.ensure((size_t)ldr * lmax * sizeof(double)));
+    SC4_TRY(Mb.ensure((size_t)l2_0 * l1_0 * sizeof(double)));
+    SC4_CUDA(cudaMemsetAsync(Mr.p, 0, (size_t)ldr * lmax * sizeof(double), st));
+    double *qm = Mq.as<double>(), *rm = Mr.as<double>();
     SC4_TRY(Om.ensure((size_t)n * lmax * sizeof(T)));
     SC4_TRY(Ps.ensure((size_t)m * l2max * sizeof(T)));
     SC4_TRY(Y.ensure((size_t)m * lmax * sizeof(T)));
@@ -790,7 +885,10 @@ static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double*
     SC4_TRY(adj_block<T>(P, ps, m, l2_0, z, n, (const T*)nullptr, 0, st));
     SC4_TRY(cholqr2<T>(m, l1_0, y, m, qy, m, ws, st));
     int l1 = l1_0, l2 = l2_0;
-    SC4_TRY(singleview_W<T>(P, l1, l2, ps, qy, z, wt, ws, st));
+    // M = Psi^T Q_Y = Q_M R_M (Alg. 3 step 4)
+    SC4_TRY(gemm_tn<T, T>(m, l2, l1, 1.0, ps, m, qy, m, 0.0, Mb.as<double>(), l2, st));
+    SC4_TRY(qr_f64(l2, l1, Mb.as<double>(), l2, qm, ldq, rm, ldr, st));
+    SC4_TRY(singleview_W<T>(P, l1, l2, qm, ldq, rm, ldr, z, wt, ws, st));
     if (adapt) {
       double kap;
       int t = 1;
@@ -814,9 +912,11 @@ static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double*
           ws2.release();
           SC4_TRY(s2);
         }
+        // Alg. 6: QR of [Psi Psi_hat]^T [Q_Y Q_Y_hat] from the QR of Psi^T Q_Y
+        SC4_TRY(qr_update<T>(m, l2, lh2, l1, lh1, ps, m, qy, m, qm, ldq, rm, ldr, st));
         l1 += lh1;
         l2 += lh2;
-        SC4_TRY(singleview_W<T>(P, l1, l2, ps, qy, z, wt, ws, st));
+        SC4_TRY(singleview_W<T>(P, l1, l2, qm, ldq, rm, ldr, z, wt, ws, st));
         SC4_TRY(kappa_remark1<T>(P, l1, wt, n, o.seed, s_ka, t++, o.prec, ws, &kap, st));
       }
     }
@@ -827,7 +927,7 @@ static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double*
   int rc = body();
   cudaStreamSynchronize(st);
   ws.release(); Om.release(); Ps.release(); Y.release(); QY.release(); Z.release(); Wt.release();
-  tmp.release();
+  tmp.release(); Mq.release(); Mr.release(); Mb.release();
   return rc;
 }
 
@@ -1516,6 +1616,17 @@ int sc4dvar_sketchsolv(sc4dvar_precond_t pc, const double* g, double* dv, void* 
   SC4_TRY(woodbury_apply(pc->n, pc->l, 1, pc->V, pc->n, pc->dsc, g, pc->n, dv, pc->n,
                          pc->T.as<double>(), S(stream)));
   return axpby<double, double>(pc->n, 0.0, dv, -1.0, dv, S(stream));
+}
+
+int sc4dvar_qr_update(int m, int r1, int r2, int k1, int k2, const double* Pm, int ldp, const double* B,
+                      int ldb, double* Q, int ldq, double* R, int ldr, void* stream) {
+  SC4_ARG(m >= 0 && r1 >= 0 && r2 >= 0 && k1 >= 0 && k2 >= 0, "qr_update: negative size");
+  SC4_ARG(r1 >= k1 && r1 + r2 >= k1 + k2, "qr_update: needs r1 >= k1 and r1 + r2 >= k1 + k2 (thin QR)");
+  SC4_ARG(Pm && B && Q && R, "qr_update: null argument");
+  SC4_ARG(ldp >= std::max(m, 1) && ldb >= std::max(m, 1) && ldq >= std::max(r1 + r2, 1) &&
+              ldr >= std::max(k1 + k2, 1),
+          "qr_update: leading dimensions");
+  return qr_update<double>(m, r1, r2, k1, k2, Pm, ldp, B, ldb, Q, ldq, R, ldr, S(stream));
 }
 
 // ------------------------------------------------------------------ line search

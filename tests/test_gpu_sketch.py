@@ -193,3 +193,65 @@ def test_gauss_newton_sketchsolv_matches_oracle(method):
     assert rel(v.cpu().numpy(), vr) <= 1e-8
     c = prob.counters()
     assert c["tlm_online"] == 0 and c["adj_online"] == 3
+
+
+@pytest.mark.parametrize("m,r1,r2,k1,k2", [
+    (300, 41, 20, 20, 10),    # A2 B1 wide (r2 < k1 + ...), the usual growth round
+    (257, 17, 16, 8, 8),      # r2 = 2 k2 as in Alg. 5 with l2 = 2 l1 + 1
+    (500, 33, 40, 16, 20),    # A2 B1 tall (r2 > k1)
+    (128, 25, 0, 12, 6),      # no new rows: only steps 4-7
+    (128, 25, 10, 12, 0),     # no new columns: only steps 1-3
+])
+def test_qr_update_matches_oracle(m, r1, r2, k1, k2):
+    """Alg. 6 through the C ABI against the oracle's restatement: R up to the
+    signs of its rows (Q up to the same column signs), Q R = [A1; A2][B1 B2]
+    and Q orthonormal."""
+    import paper_2401_15758_gb300 as g
+    from oracle import sketch
+    rng = np.random.default_rng(m + r1 + r2 + k1 + k2)
+    P = rng.standard_normal((m, r1 + r2))
+    B, _ = np.linalg.qr(rng.standard_normal((m, k1 + k2)))
+    A1, A2, B1, B2 = P[:, :r1].T, P[:, r1:].T, B[:, :k1], B[:, k1:]
+    Q1, R1 = np.linalg.qr(A1 @ B1)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    Q, R = g.qr_update(dev(P), dev(B), dev(Q1), dev(R1), r1, k1)
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    Qo, Ro = sketch.qr_update(A1, A2, B1, B2, Q1, R1)
+    assert np.all(np.tril(R, -1) == 0.0)
+    D = np.sign(np.diag(R)) * np.sign(np.diag(Ro))
+    scale = np.abs(Ro).max()
+    assert np.abs(D[:, None] * R - Ro).max() <= 1e-12 * scale
+    assert np.abs(Q * D - Qo).max() <= 1e-12 * max(1.0, scale / np.abs(np.diag(Ro)).min())
+    assert np.abs(Q @ R - P.T @ B).max() <= 1e-12 * scale
+    assert np.abs(Q.T @ Q - np.eye(k1 + k2)).max() <= 1e-13
+
+
+def test_qr_update_rejects_bad_sizes():
+    import paper_2401_15758_gb300 as g
+    z = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(g.Sc4dvarError) as e:     # r1 < k1: no thin QR of A1 B1
+        g.check(g.lib.sc4dvar_qr_update(8, 2, 2, 3, 1, g._ptr(z), 8, g._ptr(z), 8, g._ptr(z), 8,
+                                        g._ptr(z), 8, None))
+    assert e.value.code == g._abi.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adaptive_singleview_matches_oracle(small, prec):
+    """Alg. 5 with the Alg. 6 QR update on the GPU against the oracle's Alg. 5
+    (direct QR of each grown M), growing 8 -> 24 columns (l_hat = 4, l2 = 2 l + 1
+    growing by 2 l_hat): the action of H_hat, the rank and the PDE-solve counts."""
+    import paper_2401_15758_gb300 as g
+    from oracle import solvers
+    wl, prob, ref = small
+    o = solvers.GNOptions(method="singleview", adaptive=True, l=8, l_hat=4, eps_sk=0.5, l_max=24,
+                          seed=wl.seed)
+    lr = solvers.build_sketch(ref, o, 0)
+    prob.counters_reset()
+    pc = prob.build_precond("singleview", l=8, adaptive=True, l_hat=4, eps_sk=0.5, l_max=24,
+                            seed=wl.seed, prec=g.FP64 if prec == "fp64" else g.FP32)
+    c = prob.counters()
+    V, lam = pc.arrays()
+    X = np.random.default_rng(11).standard_normal((wl.n, 4))
+    tol = 1e-8 if prec == "fp64" else 1e-4
+    assert rel(hhat_action(V, lam, X), hhat_action(lr.V, lr.lam, X)) <= tol
+    assert (c["tlm_offline"], c["adj_offline"]) == (lr.tlm, lr.adj) == (24, 49)
