@@ -38,6 +38,7 @@ METRIC = ("GN Hessian-vector products/s (block k) and GN-step time to 1e-6 rel. 
 WORKLOAD = "burgers_n8192"
 K_BLOCK = 128
 FP32_PEAK_ALU = 152 * 128 * 2 * 2.070e9   # FMA lanes x 2 flops x max SM clock (flop/s)
+FP64_PEAK_FMA = 1.20e12   # FP64 FMA throughput measured by a microbenchmark on the same GB300s (flop/s)
 # Algorithmic FP32 flops per grid point per RK4 step of one direction, counted
 # from the tangent-linear / adjoint formulas of the sweeps (base-state stage
 # recomputation not counted): TLM 52, ADJ 55.
@@ -553,22 +554,37 @@ def gyre_arm(args):
     clk = clocks.stop()
     x1 = X[:1].contiguous()
     t1 = timed(lambda: p.gn_hessian_apply_block(x1))
+    # GN-step time to a 1e-6 residual at the background: FP32 RandSVD sketch of
+    # the paper's size + mixed-precision PCG against plain FP64 CG
+    gn = None if args.no_gn_step else gn_step(torch, g, p, wl, dev, sketch={"method": "randsvd", "l": wl.k})
     p.close()
     print(f"block k={wl.k}: FP64 {1e3 * t:.2f} ms, FP32 {1e3 * t32:.2f} ms; one FP64 product {1e3 * t1:.3f} ms",
           file=sys.stderr, flush=True)
-    rows = paper_runs(torch, dev, problem, wl.n, "T4", runs, iters=args.gn_iters, tol=wl.pcg_tol)
+    rows = (paper_runs(torch, dev, problem, wl.n, "T4", runs, iters=args.gn_iters, tol=wl.pcg_tol)
+            if args.gn_iters > 0 else None)
+    # flops of the sine transforms (the dense nx x nx products of every row): 12
+    # per RK3 step (a Poisson solve per stage in each sweep, two transforms
+    # each) and 4 for the two prior applies, 2 ny nx^2 flops per field each
+    dst_flops = (12 * wl.n_steps + 4) * 2.0 * wl.ny * wl.nx * wl.nx * wl.k
     out = {"metric": METRIC, "value": wl.k / t, "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "roofline": {"bound": "alu", "kernel": "block Hessian product (all kernels; sine-transform flops)",
+                        "achieved": dst_flops / t / 1e12, "peak": FP64_PEAK_FMA / 1e12, "unit": "TFLOP/s",
+                        "frac": dst_flops / t / FP64_PEAK_FMA, "traffic": None,
+                        "peak_source": "FP64 FMA microbenchmark on the pool's GB300 (1.20 TFLOP/s)"},
            "config": {"workload": f"{wl.name}: double-gyre vorticity {wl.nx}x{wl.ny} (Dirichlet), "
                                   f"Re={wl.re}, Ro={wl.ro}, RK3-TVD, {wl.n_steps} steps, m={wl.m}, "
                                   f"block k={wl.k}, FP64",
                       "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": wl.k, "gn_iters": args.gn_iters,
                       "l2": "256 MiB write before every timed step"},
-           "fp32_block": {"value": wl.k / t32, "unit": "HVP/s", "ms_per_step": 1e3 * t32},
+           "fp32_block": {"value": wl.k / t32, "unit": "HVP/s", "ms_per_step": 1e3 * t32,
+                          "roofline": {"bound": "alu", "achieved": dst_flops / t32 / 1e12,
+                                       "peak": FP32_PEAK_ALU / 1e12, "unit": "TFLOP/s",
+                                       "frac": dst_flops / t32 / FP32_PEAK_ALU}},
            "single_fp64_product_ms": 1e3 * t1,
            "gpu_launches_per_step": int(launches), "clocks": clk,
-           "paper_table4_comparison": rows}
+           "gn_step": gn, "paper_table4_comparison": rows}
     print(json.dumps(out), flush=True)
 
 
@@ -789,10 +805,30 @@ def profile_case_bve(name="bve_n256"):
     print("bve profile case done")
 
 
+def profile_case_gyre():
+    """One FP32 TLM block and one FP32 ADJ block (k = 384) of the double-gyre
+    workload over its 40-step window."""
+    import torch
+    import paper_2401_15758_gb300 as g
+    import sc4dvar_inputs as si
+    wl = si.gyre_workload()
+    d = si.gyre_draws(wl)
+    prob = g.Problem.from_gyre_workload(wl, d)
+    prob.set_background(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
+    prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
+    X = torch.tensor(si.gaussian_matrix(wl.seed, wl.k, wl.n, stream=29), device="cuda", dtype=torch.float32)
+    W = prob.tlm_block(X, prec=g.FP32)
+    prob.adj_block(W, prec=g.FP32)
+    torch.cuda.synchronize()
+    print("gyre profile case done")
+
+
 def main():
     args = parse()
     if args.profile:
-        if args.workload in ("bve_n256", "bve_n1024"):
+        if args.workload == "bve_gyre":
+            profile_case_gyre()
+        elif args.workload in ("bve_n256", "bve_n1024"):
             profile_case_bve(args.workload)
         else:
             profile_case()

@@ -90,8 +90,18 @@ __global__ void gy_dst_simple_kernel(int nx, int ny, int rows, const TI* __restr
   const int r = (int)(e / nx), p = (int)(e % nx);
   const int c = r / ny, j = r - c * ny;
   const TI* row = in + (size_t)c * ldi + (size_t)j * nx;
-  TC acc = TC(0);
-  for (int i = 0; i < nx; ++i) acc += (TC)row[i] * Sm[(size_t)i * nx + p];
+  // four partial sums: a quarter of the dependent FMA chain (this form runs for
+  // few rows, where the chain latency, not throughput, sets the time)
+  TC a0 = TC(0), a1 = TC(0), a2 = TC(0), a3 = TC(0);
+  int i = 0;
+  for (; i + 3 < nx; i += 4) {
+    a0 += (TC)row[i] * Sm[(size_t)i * nx + p];
+    a1 += (TC)row[i + 1] * Sm[(size_t)(i + 1) * nx + p];
+    a2 += (TC)row[i + 2] * Sm[(size_t)(i + 2) * nx + p];
+    a3 += (TC)row[i + 3] * Sm[(size_t)(i + 3) * nx + p];
+  }
+  for (; i < nx; ++i) a0 += (TC)row[i] * Sm[(size_t)i * nx + p];
+  TC acc = (a0 + a1) + (a2 + a3);
   const size_t o = (size_t)j * nx + p;
   if (Z) acc += (TC)Z[(size_t)c * ldz + o];
   out[(size_t)c * ldo + o] = (TO)acc;
@@ -184,11 +194,27 @@ int dst_rows(const GyreGeom& g, int k, const TI* in, int ldi, const TC* Sm, TO* 
   return SC4DVAR_OK;
 }
 
+// One element (4 or 8 bytes, naturally aligned) copied global -> shared
+// asynchronously; the copies of a thread stay in flight together.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 // In place, for each field and x-mode p: solve the tridiagonal system along y
 // (diagonal 1/piv_j after elimination, off-diagonal off). One CTA per (field,
-// slab of PW modes), the slab staged in shared memory; thread pp sweeps mode
-// p0 + pp forward (z_j = (r_j - off z_{j-1}) / piv_j) and back
-// (x_j = z_j - c'_j x_{j+1}).
+// slab of PW modes). The slab is staged in shared memory by asynchronous copies
+// (all in flight at once: a load-then-store loop would wait one memory latency
+// per row). Thread pp sweeps mode p0 + pp forward (z_j = (r_j - off z_{j-1}) /
+// piv_j) and back (x_j = z_j - c'_j x_{j+1}); the factors of the next kTh rows
+// are loaded into registers while the current kTh rows are swept.
+constexpr int kTh = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(128) gy_thomas_kernel(int nx, int ny, int PW, T* F, int ldf,
                                                         const T* __restrict__ fac, T off) {
@@ -199,24 +225,57 @@ __global__ void __launch_bounds__(128) gy_thomas_kernel(int nx, int ny, int PW, 
   T* f = F + (size_t)c * ldf;
   for (int e = threadIdx.x; e < ny * PW; e += blockDim.x) {
     const int j = e / PW, pp = e - j * PW;
-    s[e] = f[(size_t)j * nx + p0 + pp];
+    cp_async_elem(s + e, f + (size_t)j * nx + p0 + pp);
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   for (int pp = threadIdx.x; pp < PW; pp += blockDim.x) {
     const T* ipiv = fac + p0 + pp;
     const T* cpr = fac + (size_t)nx * ny + p0 + pp;
-    T z = s[pp] * ipiv[0];
-    s[pp] = z;
-#pragma unroll 8
-    for (int j = 1; j < ny; ++j) {
-      z = (s[j * PW + pp] - off * z) * ipiv[(size_t)j * nx];
-      s[j * PW + pp] = z;
+    T* sc = s + pp;
+    T cur[kTh], nxt[kTh];
+#pragma unroll
+    for (int u = 0; u < kTh; ++u) cur[u] = (u < ny) ? ipiv[(size_t)u * nx] : T(0);
+    T z = T(0);
+    for (int j0 = 0; j0 < ny; j0 += kTh) {
+#pragma unroll
+      for (int u = 0; u < kTh; ++u) {
+        const int j = j0 + kTh + u;
+        nxt[u] = (j < ny) ? ipiv[(size_t)j * nx] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kTh; ++u) {
+        const int j = j0 + u;
+        if (j < ny) {
+          z = (sc[j * PW] - off * z) * cur[u];
+          sc[j * PW] = z;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kTh; ++u) cur[u] = nxt[u];
     }
+    // x_{ny-1} = z_{ny-1}, then j = ny-2 .. 0
     T x = z;
-#pragma unroll 8
-    for (int j = ny - 2; j >= 0; --j) {
-      x = s[j * PW + pp] - cpr[(size_t)j * nx] * x;
-      s[j * PW + pp] = x;
+    const int jt = ny - 2;
+#pragma unroll
+    for (int u = 0; u < kTh; ++u) cur[u] = (jt - u >= 0) ? cpr[(size_t)(jt - u) * nx] : T(0);
+    for (int j0 = jt; j0 >= 0; j0 -= kTh) {
+#pragma unroll
+      for (int u = 0; u < kTh; ++u) {
+        const int j = j0 - kTh - u;
+        nxt[u] = (j >= 0) ? cpr[(size_t)j * nx] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kTh; ++u) {
+        const int j = j0 - u;
+        if (j >= 0) {
+          x = sc[j * PW] - cur[u] * x;
+          sc[j * PW] = x;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kTh; ++u) cur[u] = nxt[u];
     }
   }
   __syncthreads();
