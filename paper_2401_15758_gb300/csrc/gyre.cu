@@ -23,6 +23,8 @@
 // stored theta_j.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <type_traits>
 #include <vector>
 #include "common.cuh"
 #include "gyre.cuh"
@@ -169,6 +171,139 @@ __global__ void __launch_bounds__(kTileThreads) gy_dst_tiled_kernel(int nx, int 
   }
 }
 
+// Tensor-core form for FP32 fields with nx = 128 (the row transform is a dense
+// rows x 128 by 128 x 128 product): mma.sync m16n8k8 TF32 in the split form of
+// Ootomo & Yokota (2022), a = a_hi + a_lo with a_hi = tf32(a), a_lo =
+// tf32(a - a_hi), and a b ~ a_lo b_hi + a_hi b_lo + a_hi b_hi accumulated in
+// FP32 (the dropped a_lo b_lo is below FP32 rounding), which keeps FP32
+// accuracy. A persistent CTA holds S in shared memory and walks tiles of 128
+// rows, the next tile arriving by asynchronous copies into the second buffer
+// while the current one is multiplied; 16 warps, each a 32 x 32 block of the
+// 128 x 128 output tile, the three products of a k-step issued as three passes
+// over the 8 independent accumulator tiles. Row strides are padded (132 and
+// 136 words) so the fragment reads of a warp hit 32 distinct banks.
+constexpr int kTcN = 128, kTcLdA = 132, kTcLdB = 136;
+
+size_t tc_smem() { return (2 * (size_t)kTcN * kTcLdA + (size_t)kTcN * kTcLdB) * 4; }
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// rows r0 .. r0+127 of the input into a padded tile; rows past the end read as
+// zero (source size 0)
+__device__ __forceinline__ void tc_load_tile(float* dst, const float* __restrict__ in, int ldi, int ny,
+                                             int rows, int r0) {
+  for (int e = threadIdx.x; e < kTcN * (kTcN / 4); e += blockDim.x) {
+    const int rr = e >> 5, q = e & 31, r = r0 + rr;
+    const float* src = in;
+    int bytes = 0;
+    if (r < rows) {
+      const int c = r / ny, j = r - c * ny;
+      src = in + (size_t)c * ldi + (size_t)j * kTcN + 4 * q;
+      bytes = 16;
+    }
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst + rr * kTcLdA + 4 * q);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(512, 1) gy_dst_tf32x3_kernel(int ny, int rows, const float* __restrict__ in,
+                                                               int ldi, const float* __restrict__ Sm,
+                                                               float* __restrict__ out, int ldo) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* sA = reinterpret_cast<float*>(smraw);  // [2][128][kTcLdA] input tiles
+  float* sB = sA + 2 * kTcN * kTcLdA;           // [128][kTcLdB] S
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = warp >> 2, wn = warp & 3;  // warp block: rows 32 wm.., columns 32 wn..
+  const int tiles = (rows + kTcN - 1) / kTcN;
+  if ((int)blockIdx.x < tiles) tc_load_tile(sA, in, ldi, ny, rows, blockIdx.x * kTcN);
+  for (int e = tid; e < kTcN * kTcN; e += blockDim.x) sB[(e >> 7) * kTcLdB + (e & 127)] = Sm[e];
+  int it = 0;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    const float* cA = sA + (it & 1) * kTcN * kTcLdA;
+    const int nxt = tile + gridDim.x;
+    if (nxt < tiles) {
+      tc_load_tile(sA + ((it + 1) & 1) * kTcN * kTcLdA, in, ldi, ny, rows, nxt * kTcN);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();  // this tile (and S) visible to every warp
+    float acc[2][4][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[mi][ni][q] = 0.f;
+#pragma unroll 1
+    for (int k0 = 0; k0 < kTcN; k0 += 8) {
+      uint32_t bh[4][2], bl[4][2], ah[2][4], al[2][4];
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const int col = wn * 32 + ni * 8 + g;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float v = sB[(k0 + t + 4 * h) * kTcLdB + col];
+          bh[ni][h] = tf32_rna(v);
+          bl[ni][h] = tf32_rna(v - __uint_as_float(bh[ni][h]));
+        }
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const float* a0p = cA + (wm * 32 + mi * 16 + g) * kTcLdA + k0 + t;
+        const float x[4] = {a0p[0], a0p[8 * kTcLdA], a0p[4], a0p[8 * kTcLdA + 4]};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ah[mi][q] = tf32_rna(x[q]);
+          al[mi][q] = tf32_rna(x[q] - __uint_as_float(ah[mi][q]));
+        }
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(acc[mi][ni], al[mi], bh[ni]);
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(acc[mi][ni], ah[mi], bl[ni]);
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(acc[mi][ni], ah[mi], bh[ni]);
+    }
+    const int r0 = tile * kTcN;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = r0 + wm * 32 + mi * 16 + g + 8 * h;
+        if (r >= rows) continue;
+        const int c = r / ny, j = r - c * ny;
+        float* orow = out + (size_t)c * ldo + (size_t)j * kTcN;
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+          const int col = wn * 32 + ni * 8 + 2 * t;
+          orow[col] = acc[mi][ni][2 * h];
+          orow[col + 1] = acc[mi][ni][2 * h + 1];
+        }
+      }
+    __syncthreads();  // every warp done with this buffer before it is refilled
+  }
+}
+
 size_t tiled_smem(int nx, size_t tb) {
   const int CG = nx / 8, BR = 4 * (kTileThreads / CG);
   return ((size_t)kBK * (BR + 4) + (size_t)kBK * nx) * tb;
@@ -179,6 +314,20 @@ int dst_rows(const GyreGeom& g, int k, const TI* in, int ldi, const TC* Sm, TO* 
              int ldz, cudaStream_t st) {
   const int nx = g.nx, rows = k * g.ny;
   if (rows <= 0) return SC4DVAR_OK;
+  if constexpr (std::is_same<TI, float>::value && std::is_same<TC, float>::value &&
+                std::is_same<TO, float>::value) {
+    // tensor-core form: nx = 128, no added term, 16-byte aligned input rows,
+    // at least 16 tiles of 128 rows
+    const int tiles = div_up(rows, kTcN);
+    if (nx == kTcN && Z == nullptr && ((uintptr_t)in % 16) == 0 && ldi % 4 == 0 && tiles >= 16) {
+      const size_t smem = tc_smem();
+      SC4_CUDA(cudaFuncSetAttribute(gy_dst_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      gy_dst_tf32x3_kernel<<<std::min(tiles, 152), 512, smem, st>>>(g.ny, rows, in, ldi, Sm, out, ldo);
+      SC4_LAUNCH_CHECK();
+      return SC4DVAR_OK;
+    }
+  }
   const int BR = 4 * (kTileThreads / std::max(1, nx / 8));
   if (nx >= 16 && div_up(rows, BR) >= 152) {
     const size_t smem = tiled_smem(nx, sizeof(TC));
@@ -194,103 +343,89 @@ int dst_rows(const GyreGeom& g, int k, const TI* in, int ldi, const TC* Sm, TO* 
   return SC4DVAR_OK;
 }
 
-// One element (4 or 8 bytes, naturally aligned) copied global -> shared
-// asynchronously; the copies of a thread stay in flight together.
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
-  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-
 // In place, for each field and x-mode p: solve the tridiagonal system along y
-// (diagonal 1/piv_j after elimination, off-diagonal off). One CTA per (field,
-// slab of PW modes). The slab is staged in shared memory by asynchronous copies
-// (all in flight at once: a load-then-store loop would wait one memory latency
-// per row). Thread pp sweeps mode p0 + pp forward (z_j = (r_j - off z_{j-1}) /
-// piv_j) and back (x_j = z_j - c'_j x_{j+1}); the factors of the next kTh rows
-// are loaded into registers while the current kTh rows are swept.
+// (diagonal 1/piv_j after elimination, off-diagonal off). One thread per
+// (field, mode): the recurrences run down the rows in global memory, a warp's
+// 32 modes reading and writing 32 consecutive words of a row. Rows (and their
+// factors) are loaded kTh at a time into registers one chunk ahead of the
+// recurrence, so the dependent chain is only the arithmetic and the loads of
+// the next chunk overlap it: forward z_j = (r_j - off z_{j-1}) / piv_j, back
+// x_j = z_j - c'_j x_{j+1}.
 constexpr int kTh = 16;
 
 template <typename T>
-__global__ void __launch_bounds__(128) gy_thomas_kernel(int nx, int ny, int PW, T* F, int ldf,
+__global__ void __launch_bounds__(128) gy_thomas_kernel(int nx, int ny, int k, T* F, int ldf,
                                                         const T* __restrict__ fac, T off) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* s = reinterpret_cast<T*>(smraw);  // [ny][PW]
-  const int slabs = nx / PW;
-  const int c = blockIdx.x / slabs, p0 = (blockIdx.x - c * slabs) * PW;
-  T* f = F + (size_t)c * ldf;
-  for (int e = threadIdx.x; e < ny * PW; e += blockDim.x) {
-    const int j = e / PW, pp = e - j * PW;
-    cp_async_elem(s + e, f + (size_t)j * nx + p0 + pp);
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= k * nx) return;
+  const int c = gid / nx, p = gid - c * nx;
+  T* f = F + (size_t)c * ldf + p;
+  const T* ipv = fac + p;
+  const T* cpr = fac + (size_t)nx * ny + p;
+  T r[kTh], q[kTh], rn[kTh], qn[kTh];
+#pragma unroll
+  for (int u = 0; u < kTh; ++u) {
+    r[u] = (u < ny) ? f[(size_t)u * nx] : T(0);
+    q[u] = (u < ny) ? ipv[(size_t)u * nx] : T(0);
   }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
-  for (int pp = threadIdx.x; pp < PW; pp += blockDim.x) {
-    const T* ipiv = fac + p0 + pp;
-    const T* cpr = fac + (size_t)nx * ny + p0 + pp;
-    T* sc = s + pp;
-    T cur[kTh], nxt[kTh];
+  T z = T(0);
+  for (int j0 = 0; j0 < ny; j0 += kTh) {
 #pragma unroll
-    for (int u = 0; u < kTh; ++u) cur[u] = (u < ny) ? ipiv[(size_t)u * nx] : T(0);
-    T z = T(0);
-    for (int j0 = 0; j0 < ny; j0 += kTh) {
-#pragma unroll
-      for (int u = 0; u < kTh; ++u) {
-        const int j = j0 + kTh + u;
-        nxt[u] = (j < ny) ? ipiv[(size_t)j * nx] : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < kTh; ++u) {
-        const int j = j0 + u;
-        if (j < ny) {
-          z = (sc[j * PW] - off * z) * cur[u];
-          sc[j * PW] = z;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kTh; ++u) cur[u] = nxt[u];
+    for (int u = 0; u < kTh; ++u) {
+      const int j = j0 + kTh + u;
+      rn[u] = (j < ny) ? f[(size_t)j * nx] : T(0);
+      qn[u] = (j < ny) ? ipv[(size_t)j * nx] : T(0);
     }
-    // x_{ny-1} = z_{ny-1}, then j = ny-2 .. 0
-    T x = z;
-    const int jt = ny - 2;
 #pragma unroll
-    for (int u = 0; u < kTh; ++u) cur[u] = (jt - u >= 0) ? cpr[(size_t)(jt - u) * nx] : T(0);
-    for (int j0 = jt; j0 >= 0; j0 -= kTh) {
-#pragma unroll
-      for (int u = 0; u < kTh; ++u) {
-        const int j = j0 - kTh - u;
-        nxt[u] = (j >= 0) ? cpr[(size_t)j * nx] : T(0);
+    for (int u = 0; u < kTh; ++u)
+      if (j0 + u < ny) {
+        z = (r[u] - off * z) * q[u];
+        r[u] = z;
       }
 #pragma unroll
-      for (int u = 0; u < kTh; ++u) {
-        const int j = j0 - u;
-        if (j >= 0) {
-          x = sc[j * PW] - cur[u] * x;
-          sc[j * PW] = x;
-        }
-      }
+    for (int u = 0; u < kTh; ++u)
+      if (j0 + u < ny) f[(size_t)(j0 + u) * nx] = r[u];
 #pragma unroll
-      for (int u = 0; u < kTh; ++u) cur[u] = nxt[u];
+    for (int u = 0; u < kTh; ++u) {
+      r[u] = rn[u];
+      q[u] = qn[u];
     }
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < ny * PW; e += blockDim.x) {
-    const int j = e / PW, pp = e - j * PW;
-    f[(size_t)j * nx + p0 + pp] = s[e];
+  T x = z;  // x_{ny-1} = z_{ny-1}
+  const int jt = ny - 2;
+#pragma unroll
+  for (int u = 0; u < kTh; ++u) {
+    r[u] = (jt - u >= 0) ? f[(size_t)(jt - u) * nx] : T(0);
+    q[u] = (jt - u >= 0) ? cpr[(size_t)(jt - u) * nx] : T(0);
+  }
+  for (int j0 = jt; j0 >= 0; j0 -= kTh) {
+#pragma unroll
+    for (int u = 0; u < kTh; ++u) {
+      const int j = j0 - kTh - u;
+      rn[u] = (j >= 0) ? f[(size_t)j * nx] : T(0);
+      qn[u] = (j >= 0) ? cpr[(size_t)j * nx] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kTh; ++u)
+      if (j0 - u >= 0) {
+        x = r[u] - q[u] * x;
+        r[u] = x;
+      }
+#pragma unroll
+    for (int u = 0; u < kTh; ++u)
+      if (j0 - u >= 0) f[(size_t)(j0 - u) * nx] = r[u];
+#pragma unroll
+    for (int u = 0; u < kTh; ++u) {
+      r[u] = rn[u];
+      q[u] = qn[u];
+    }
   }
 }
 
 template <typename T>
 int thomas(const GyreGeom& g, int k, T* F, int ldf, const T* fac, double off, cudaStream_t st) {
-  const int PW = std::min(g.nx, sizeof(T) == 4 ? 128 : 64);
-  const size_t smem = (size_t)g.ny * PW * sizeof(T);
-  SC4_CUDA(cudaFuncSetAttribute(gy_thomas_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  gy_thomas_kernel<T><<<k * (g.nx / PW), 128, smem, st>>>(g.nx, g.ny, PW, F, ldf, fac, (T)off);
+  if (k <= 0) return SC4DVAR_OK;
+  gy_thomas_kernel<T><<<div_up(k * g.nx, 128), 128, 0, st>>>(g.nx, g.ny, k, F, ldf, fac, (T)off);
   SC4_LAUNCH_CHECK();
   return SC4DVAR_OK;
 }
