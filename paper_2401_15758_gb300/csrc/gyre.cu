@@ -37,7 +37,7 @@ constexpr int kTileThreads = 256;
 
 template <typename T>
 struct GyP {
-  int nx, ny, n;
+  int nx, ny, n, lnx;  // nx = 2^lnx
   T inv2h, invh2, re_inv, ro_inv;
 };
 
@@ -47,6 +47,8 @@ GyP<T> make_p(const GyreGeom& g) {
   p.nx = g.nx;
   p.ny = g.ny;
   p.n = g.n;
+  p.lnx = 0;
+  while ((1 << p.lnx) < g.nx) ++p.lnx;
   p.inv2h = (T)(1.0 / (2.0 * g.h));
   p.invh2 = (T)(1.0 / (g.h * g.h));
   p.re_inv = (T)g.re_inv;
@@ -514,10 +516,10 @@ struct TlmStage {
 template <typename T>
 __global__ void gy_tlm_stage_kernel(GyP<T> p, int k, const T* __restrict__ om_b, const T* __restrict__ ps_b,
                                     TlmStage<T> a) {
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)k * p.n) return;
-  const int c = (int)(e / p.n), q = (int)(e - (size_t)c * p.n);
-  const int j = q / p.nx, i = q - j * p.nx;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = field
+  if (q >= p.n || (int)blockIdx.y >= k) return;
+  const int c = blockIdx.y;
+  const int j = q >> p.lnx, i = q & (p.nx - 1);
   const size_t off = (size_t)c * p.n;
   const T* X = a.dX + off;
   const T* dp = a.dpsi + off;
@@ -544,10 +546,10 @@ __global__ void gy_tlm_stage_kernel(GyP<T> p, int k, const T* __restrict__ om_b,
 // first half: g = D_y(omega_b,x kappa) - D_x(omega_b,y kappa) - Ro^{-1} D_x kappa
 template <typename T>
 __global__ void gy_adj_pre_kernel(GyP<T> p, int k, const T* __restrict__ om_b, Comb<T> kap, T* __restrict__ gout) {
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)k * p.n) return;
-  const int c = (int)(e / p.n), q = (int)(e - (size_t)c * p.n);
-  const int j = q / p.nx, i = q - j * p.nx;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = field
+  if (q >= p.n || (int)blockIdx.y >= k) return;
+  const int c = blockIdx.y;
+  const int j = q >> p.lnx, i = q & (p.nx - 1);
   const size_t off = (size_t)c * p.n;
   auto obx = [&](int ii, int jj) { return (at(om_b, ii + 1, jj, p) - at(om_b, ii - 1, jj, p)) * p.inv2h; };
   auto oby = [&](int ii, int jj) { return (at(om_b, ii, jj + 1, p) - at(om_b, ii, jj - 1, p)) * p.inv2h; };
@@ -571,10 +573,10 @@ struct AdjPost {
 template <typename T>
 __global__ void gy_adj_post_kernel(GyP<T> p, int k, const T* __restrict__ ps_b, Comb<T> kap, AdjPost<T> a,
                                    int S) {
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)k * p.n) return;
-  const int c = (int)(e / p.n), q = (int)(e - (size_t)c * p.n);
-  const int j = q / p.nx, i = q - j * p.nx;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = field
+  if (q >= p.n || (int)blockIdx.y >= k) return;
+  const int c = blockIdx.y;
+  const int j = q >> p.lnx, i = q & (p.nx - 1);
   const size_t off = (size_t)c * p.n;
   auto pbx = [&](int ii, int jj) { return (at(ps_b, ii + 1, jj, p) - at(ps_b, ii - 1, jj, p)) * p.inv2h; };
   auto pby = [&](int ii, int jj) { return (at(ps_b, ii, jj + 1, p) - at(ps_b, ii, jj - 1, p)) * p.inv2h; };
@@ -772,6 +774,7 @@ int gyre_fwd(const GyreGeom& g, const double* x0, bool store, const double* y, d
 template <typename T>
 int gyre_tlm(const GyreGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void* ws, cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
+  SC4_ARG(k <= 65535, "double gyre: at most 65535 directions per sweep (one grid row per direction)");
   const int n = g.n;
   const size_t fb = field_bytes(g, k, sizeof(T));
   char* w = static_cast<char*>(ws);
@@ -803,7 +806,7 @@ int gyre_tlm(const GyreGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void
       }
       a.s = s;
       const size_t row = ((size_t)t * g.S + s) * n;
-      gy_tlm_stage_kernel<T><<<blocks_of((size_t)k * n), 256, 0, st>>>(p, k, om + row, ps + row, a);
+      gy_tlm_stage_kernel<T><<<dim3(blocks_of(n), k), 256, 0, st>>>(p, k, om + row, ps + row, a);
       SC4_LAUNCH_CHECK();
     }
     const int oi = g.obs_of_step_h[t + 1];
@@ -819,6 +822,7 @@ int gyre_tlm(const GyreGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void
 template <typename T>
 int gyre_adj(const GyreGeom& g, const T* W, int ldw, int k, T* Out, int ldo, void* ws, cudaStream_t st) {
   if (k <= 0) return SC4DVAR_OK;
+  SC4_ARG(k <= 65535, "double gyre: at most 65535 directions per sweep (one grid row per direction)");
   const int n = g.n;
   const size_t fb = field_bytes(g, k, sizeof(T));
   char* w = static_cast<char*>(ws);
@@ -859,7 +863,7 @@ int gyre_adj(const GyreGeom& g, const T* W, int ldw, int k, T* Out, int ldo, voi
         kap.c[q] = T(0);
       }
       const size_t row = ((size_t)(t - 1) * g.S + s) * n;
-      gy_adj_pre_kernel<T><<<blocks_of((size_t)k * n), 256, 0, st>>>(p, k, om + row, kap, gb);
+      gy_adj_pre_kernel<T><<<dim3(blocks_of(n), k), 256, 0, st>>>(p, k, om + row, kap, gb);
       SC4_LAUNCH_CHECK();
       SC4_TRY(poisson<T>(g, k, gb, phi, tmp, st));
       AdjPost<T> a{};
@@ -868,7 +872,7 @@ int gyre_adj(const GyreGeom& g, const T* W, int ldw, int k, T* Out, int ldo, voi
       a.lam_out = lam[cur ^ 1];
       for (int q = 0; q < 4; ++q) a.Th[q] = Th[q];
       a.s = s;
-      gy_adj_post_kernel<T><<<blocks_of((size_t)k * n), 256, 0, st>>>(p, k, ps + row, kap, a, g.S);
+      gy_adj_post_kernel<T><<<dim3(blocks_of(n), k), 256, 0, st>>>(p, k, ps + row, kap, a, g.S);
       SC4_LAUNCH_CHECK();
     }
     cur ^= 1;
