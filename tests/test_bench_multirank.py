@@ -74,3 +74,19 @@ def test_reference_arm_under_torchrun_prints_one_line():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_paper_counts_tables():
+    """The paper's printed PDE-solve counts the experiment arms compare against
+    (Tables 3 and 4): every method, in the column order of the comparison rows."""
+    t3, t4 = bench.paper_counts("T3"), bench.paper_counts("T4")
+    assert set(t3) == {"Prec_Gamma", "Prec_Lanczos", "SketchPrec_RandSVD", "SketchPrec_Nystrom",
+                       "SketchPrec_SingleView", "SketchSolv_RandSVD", "SketchSolv_Nystrom",
+                       "SketchSolv_SingleView"}
+    assert set(t4) == {"Prec_Gamma", "SketchPrec_RandSVD", "SketchPrec_Nystrom", "SketchPrec_SingleView",
+                       "SketchPrecA_RandSVD", "SketchPrecA_Nystrom", "SketchPrecA_SingleView"}
+    assert t3["SketchSolv_SingleView"] == [None, 45, 93, 10, 0, 3]
+    assert t4["Prec_Gamma"] == [15441, None, None, 57, 15441, 15466]
+    # Table 4 accounting: online ADJ = PCG iterations + 25 GN gradients (+ 1 where printed so)
+    for name, row in t4.items():
+        assert row[5] - row[0] in (25, 26), name
