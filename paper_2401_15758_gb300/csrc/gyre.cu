@@ -3,9 +3,10 @@
 //
 // Every RK stage needs psi = P omega, P = h^2 (-Delta*)^{-1}. The solve is
 //   1. a sine transform of every grid row (a dense product with the nx x nx
-//      matrix S; nx <= 128, so one CTA tile holds all output modes),
-//   2. one tridiagonal (Thomas) solve along y per x-mode, on a shared-memory
-//      copy of the field,
+//      matrix S; nx <= 128, so one CTA tile holds all output modes; FP32 fields
+//      at nx = 128 run it on the tensor cores in the 3xTF32 split),
+//   2. one tridiagonal (Thomas) solve along y per x-mode, one thread per
+//      (field, mode) running down the rows,
 //   3. the inverse transform (S again).
 // The stage kernels are pointwise with a one-point halo (central differences,
 // zero boundary values) and fuse the RK combinations, so one stage of k
