@@ -30,7 +30,9 @@ STREAM_SKETCH = 100
 STREAM_KAPPA = 200
 STREAM_PSI = 1000
 
-OK, BREAKDOWN, NOT_CONVERGED = 0, -5, -6
+# Same values as the library's status codes (SC4DVAR_ERR_BREAKDOWN = -4,
+# SC4DVAR_ERR_NOT_CONVERGED = -5), so statuses compare directly.
+OK, BREAKDOWN, NOT_CONVERGED = 0, -4, -5
 
 
 def pcg(op, b, precond=None, tol=1e-6, maxit=None):

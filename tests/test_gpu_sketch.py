@@ -135,21 +135,35 @@ def test_gauss_newton_matches_oracle(method):
     assert rel(v.cpu().numpy(), vr) <= 1e-5
 
 
-def test_adaptive_reuse_gauss_newton_matches_oracle():
+def _reuse_pair(wl, eps_re):
     from oracle import solvers
-    wl = si.burgers_workload("burgers_n128")
     prob, ref = make_pair(wl)
     v = torch.zeros(wl.n, dtype=torch.float64, device="cuda")
-    rec = prob.gauss_newton(v, iters=3, method="randsvd", l=8, adaptive=True, tol=1e-6)
+    rec = prob.gauss_newton(v, iters=3, method="randsvd", l=8, adaptive=True, eps_re=eps_re,
+                            tol=1e-6)
     vr, info = solvers.gauss_newton(ref, np.zeros(wl.n),
                                     solvers.GNOptions(iters=3, method="randsvd", l=8, adaptive=True,
-                                                      pcg_tol=1e-6))
+                                                      eps_re=eps_re, pcg_tol=1e-6))
     for a, b in zip(rec, info):
         assert a["sketched"] == b["sketched"]
         assert a["rank"] == b["l"]
         assert abs(a["J"] - b["J"]) <= 1e-9 * abs(b["J"])
         if b["kappa_re"] is not None:
             assert abs(a["kappa_re"] - b["kappa_re"]) <= 1e-8 * b["kappa_re"]
+    return rec, info
+
+
+def test_adaptive_reuse_gauss_newton_matches_oracle():
+    """The reuse rule of Sec. 3.2 (Eq. condtext2) on both sides: with the
+    paper's eps_re = 10 the later GN iterations keep the first sketch; with
+    eps_re just below the kappa_re of iteration 1 that iteration re-sketches."""
+    wl = si.burgers_workload("burgers_n128")
+    rec, info = _reuse_pair(wl, 10.0)
+    assert rec[0]["sketched"] and any(not r["sketched"] for r in rec[1:])
+    k1 = info[1]["kappa_re"]
+    assert k1 is not None and k1 < 10.0
+    rec2, info2 = _reuse_pair(wl, k1 * (1 - 1e-4))
+    assert rec2[1]["sketched"] and info2[1]["sketched"]
 
 
 @pytest.mark.parametrize("alpha1", [1.0, 3.0])

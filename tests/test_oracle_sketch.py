@@ -274,3 +274,125 @@ def test_oracle_gn_counters_follow_paper_accounting(tiny_wl):
     assert prob.counters["tlm"] == pcg + off_t
     assert prob.counters["adj"] == pcg + 3 + off_a
     assert prob.counters["fwd"] == 3
+
+
+# --------------------------------------------------------------------------- Alg. 2 shift
+def test_nystrom_shift_closed_form_on_an_invariant_subspace():
+    """Alg. 2 steps 3-7 with Omega spanning the leading eigenvectors of H:
+    Y = H Omega = Q_l D_l, so |Y|_2 = d_1 and the shift is nu = sqrt(n) eps d_1
+    (step 3); the Nystrom approximation of H + nu I on that subspace is exact,
+    so sigma^2 = d_i + nu and Lam_hat = d_i, V_hat = Q_l up to signs. A dropped
+    '- nu', a wrong norm or a wrong constant in nu breaks one of these."""
+    n, l = 40, 6
+    rng = np.random.default_rng(21)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    d = 50.0 * 0.3 ** np.arange(n)
+    H = (Q * d) @ Q.T
+    Om = Q[:, :l]
+    eps = 1e-3                                 # large, so nu is visible (nu / d_l ~ 2.6)
+    lr, nu = sketch.nystrom_core(Om, H @ Om, eps)
+    assert nu == pytest.approx(np.sqrt(n) * eps * d[0], rel=1e-13)
+    assert nu > d[l - 1]                       # the shift is not negligible here
+    assert np.allclose(lr.lam, d[:l], rtol=1e-11, atol=0)
+    assert np.allclose(np.abs(lr.V.T @ Q[:, :l]), np.eye(l), atol=1e-10)
+    # the planted mistake (no '- nu' in Lam_hat) fails the same check
+    assert not np.allclose(lr.lam + nu, d[:l], rtol=1e-6, atol=0)
+
+
+def _nystrom_shifted_dense(H, Om, nu, l):
+    """The stabilized Nystrom approximation from its definition: the Nystrom
+    approximation of H + nu I, (H + nu I) Om (Om^T (H + nu I) Om)^+ ((H + nu I) Om)^T,
+    eigen-decomposed, its l leading eigenvalues shifted back by nu and clamped at 0."""
+    n = H.shape[0]
+    Hn = H + nu * np.eye(n)
+    Yn = Hn @ Om
+    Hhat_nu = Yn @ np.linalg.pinv(Om.T @ Yn) @ Yn.T
+    mu, U = np.linalg.eigh(0.5 * (Hhat_nu + Hhat_nu.T))
+    mu, U = mu[::-1][:l], U[:, ::-1][:, :l]
+    lam = np.maximum(0.0, mu - nu)
+    return lam, (U * lam) @ U.T
+
+
+@pytest.mark.parametrize("eps", [2.0 ** -24, 1e-4])
+def test_nystrom_shift_matches_dense_definition_and_interlacing(eps):
+    """Alg. 2 with a Gaussian Omega at a reduced-precision unit roundoff (and a
+    larger one) against the definition evaluated densely; and, since the Nystrom
+    approximation of the PSD matrix H + nu I is dominated by it, every Lam_hat_i
+    is at most lambda_i(H)."""
+    n, m = 60, 45
+    j = np.arange(1, 41)
+    A = synthetic_operator(n, m, 300.0 * np.exp(-0.7 * j), 4)
+    H = A.T @ A
+    Om = philox.gaussian(7, 100, n, 10)
+    lr, nu = sketch.nystrom_core(Om, H @ Om, eps)
+    lam_d, Hhat_d = _nystrom_shifted_dense(H, Om, nu, 10)
+    scale = np.abs(H).max()
+    assert np.allclose(lr.lam, lam_d, rtol=0, atol=1e-9 * scale)
+    assert np.max(np.abs(lr.H_hat() - Hhat_d)) <= 1e-9 * scale
+    lamH = np.sort(np.linalg.eigvalsh(H))[::-1][:10]
+    assert np.all(lr.lam <= lamH + 1e-10 * scale)
+    if eps == 1e-4:
+        # nu is large enough here that the planted mistake (no '- nu') breaks
+        # both the dense definition and the interlacing bound
+        bad = lr.lam + nu
+        assert not np.allclose(bad, lam_d, rtol=0, atol=1e-9 * scale)
+        assert np.any(bad > lamH + 1e-10 * scale)
+
+
+# ------------------------------------------------------------------ reuse rule (Sec. 3.2)
+def _reuse_run(wl, eps_re, iters=3):
+    import sc4dvar_inputs as si
+    from oracle import workload
+    prob = workload.burgers_problem(wl, si.burgers_draws(wl))
+    o = solvers.GNOptions(iters=iters, method="randsvd", adaptive=True, l=4, eps_re=eps_re,
+                          pcg_tol=1e-10)
+    prob.counters = {"fwd": 0, "tlm": 0, "adj": 0}
+    v, info = solvers.gauss_newton(prob, np.zeros(wl.n), o)
+    return prob, o, v, info
+
+
+def test_gn_reuse_rule_follows_kappa_re_in_both_directions(tiny_wl):
+    """Eq. condtext2: at GN iteration k > 0 the last sketch is kept while
+    kappa_re = |(I + H^(k)) (I + H_hat^(k-i))^{-1} v|_2 < eps_re and recomputed
+    otherwise; iteration 0 always sketches. kappa_re is checked against a dense
+    evaluation of that definition (assembled H at the new iterate, dense solve
+    with the previous sketch), eps_re is then set just above and just below it,
+    and the per-iteration flags and PDE-solve counters follow."""
+    # eps_re huge: sketch once, then reuse
+    prob, o, v, info = _reuse_run(tiny_wl, 1e30)
+    assert info[0]["sketched"] and info[0]["kappa_re"] is None
+    assert [r["sketched"] for r in info[1:]] == [False, False]
+    for r in info[1:]:
+        assert r["tlm_off"] == 0 and r["adj_off"] == 0 and r["l"] == info[0]["l"]
+    # counters: one HVP per PCG iteration, per kappa_sk test of the adaptive
+    # sketch and per kappa_re test, plus the sketch columns and one gradient per
+    # GN iteration
+    from oracle import workload
+    import sc4dvar_inputs as si
+    p0 = workload.burgers_problem(tiny_wl, si.burgers_draws(tiny_wl))
+    p0.set_iterate(np.zeros(tiny_wl.n))
+    lr0 = solvers.build_sketch(p0, o, 0)
+    n_ksk = len(lr0.kappa_hist)
+    pcg = sum(r["pcg_its"] for r in info)
+    assert prob.counters["tlm"] == pcg + lr0.tlm + n_ksk + 2
+    assert prob.counters["adj"] == pcg + lr0.adj + n_ksk + 2 + 3
+
+    # kappa_re at iteration 1 from its definition
+    _, _, v1, _ = _reuse_run(tiny_wl, 1e30, iters=1)
+    p0.set_iterate(v1)
+    A1 = p0.A_dense()
+    Ip = np.eye(tiny_wl.n) + A1.T @ A1
+    vt = sketch.unit_test_vector(o.seed, solvers.STREAM_KAPPA + 1, tiny_wl.n, index=0)
+    k_dense = float(np.linalg.norm(Ip @ np.linalg.solve(np.eye(tiny_wl.n) + lr0.H_hat(), vt)))
+    k1 = info[1]["kappa_re"]
+    assert k1 == pytest.approx(k_dense, rel=1e-10)
+    assert k1 > 1.0 + 1e-6               # the Hessian moved: the rule has something to decide
+
+    # eps_re just above kappa_re: reuse; just below: re-sketch (kappa_re >= eps_re)
+    _, _, _, above = _reuse_run(tiny_wl, k1 * (1 + 1e-7), iters=2)
+    _, _, _, below = _reuse_run(tiny_wl, k1 * (1 - 1e-7), iters=2)
+    assert above[1]["kappa_re"] == pytest.approx(k1, rel=1e-12)
+    assert below[1]["kappa_re"] == pytest.approx(k1, rel=1e-12)
+    assert not above[1]["sketched"] and above[1]["tlm_off"] == 0
+    assert below[1]["sketched"] and below[1]["tlm_off"] > 0 and below[1]["adj_off"] > 0
+    assert above[0]["sketched"] and below[0]["sketched"]
