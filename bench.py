@@ -47,8 +47,8 @@ FLOPS_ADJ = 55
 KERNELS = {"tlm": "tlm_f32x2_kernel<8,false>", "adj": "adj_f32x2_kernel<8,false>"}
 # DRAM bytes (read + write) per launch of the k=128 FP32 sweeps, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 1280-step profile case
-# (bench.py --profile), scaled by the step count to the 12 800-step launch;
-# profiles/burgers_sweeps_n8192_k128.md. Set to None when the kernels change.
+# (bench.py --profile), scaled by the step count to the 12 800-step launch.
+# Set to None when the kernels change.
 TRAFFIC_PER_LAUNCH = {"tlm": (46.179328e6 + 0.123904e6) * 10, "adj": (44.090624e6 + 0.302080e6) * 10}
 
 

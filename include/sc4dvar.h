@@ -281,18 +281,21 @@ int sc4dvar_gn_hessian_apply_block(sc4dvar_problem_t p, const void* X_dev, int l
                                    void* stream);
 
 /* The same product as sc4dvar_gn_hessian_apply_block, for callers that may not
- * allocate device memory during the call (work captured into a CUDA graph, a
- * host that owns all device memory through its own pool, a loop that must not
- * enter the driver's allocator). This entry point has no counterpart in the
+ * allocate device memory during the call (a host that owns all device memory
+ * through its own pool, a loop that must not enter the driver's allocator,
+ * which can synchronize the device). This entry point has no counterpart in the
  * paper. It allocates nothing: its three work arrays (Gamma^{1/2} X, A X, the
  * adjoint state: (2 n + m) k elements of the prec type, each rounded up to 256
  * bytes) are carved from one fixed 32 MiB device array that the library holds on
  * every GPU that loads it, until the process exits. Larger k returns
  * SC4DVAR_ERR_INVALID_ARG (use sc4dvar_gn_hessian_apply_block then). The first
- * call on a device looks up that array's device address (cudaGetSymbolAddress);
- * make it before any stream capture. All calls share the array, and it keeps the
- * previous call's contents (nothing in it needs clearing): calls that overlap on
- * the GPU, on any stream or problem, race and give wrong results. */
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * and keeps it for the process; make that first call before any stream capture
+ * begins. A cudaDeviceReset frees the array with every other allocation on the
+ * device (problems included), so the entry point is not usable after one. All
+ * calls share the array, and it keeps the previous call's contents (nothing in
+ * it needs clearing): calls that overlap on the GPU, on any stream or problem,
+ * race and give wrong results. Burgers problems only. */
 int sc4dvar_gn_hessian_apply_block_noalloc(sc4dvar_problem_t p, const void* X_dev, int ldx, int k,
                                            void* Y_dev, int ldy, int misfit_only, int prec,
                                            void* stream);

@@ -3,19 +3,20 @@
 // sc4dvar_gn_hessian_apply_block needs three n x k / m x k work arrays between
 // its four kernels (Gamma^{1/2} X, A X, and the adjoint state), and the handle
 // grows them with cudaMalloc on first use or when k grows. Some callers cannot
-// allow that: code running while a CUDA graph is being captured, a host that
-// hands every byte of device memory to its own pool allocator, or a real-time
-// loop that must never hit the driver's allocator (cudaMalloc can synchronize the
-// device). This file gives them the same product with the work arrays carved
-// from one file-scope device array of fixed size. The caller still passes X and
-// Y; the library allocates nothing in this call.
+// allow that: a host that hands every byte of device memory to its own pool
+// allocator, or a real-time loop that must never enter the driver's allocator
+// (cudaMalloc can synchronize the device). This file gives them the same
+// product with the work arrays carved from one file-scope device array of fixed
+// size. The caller still passes X and Y; the library allocates nothing in this
+// call.
 //
 // The array is a static __device__ object: every GPU that loads the library
 // holds SC4_NOALLOC_SCRATCH_BYTES of it until the process exits. Host code may
 // not use the symbol as a device pointer (on the host it names a host-side
 // stand-in), so the device address is looked up with cudaGetSymbolAddress once
 // per device, with that device current, on the first call made on it. Make that
-// first call before any stream capture begins.
+// first call before any stream capture begins. A cudaDeviceReset releases the
+// array (and every problem's memory); the cached address is not valid after it.
 #include <mutex>
 #include <string>
 #include "common.cuh"
