@@ -444,6 +444,355 @@ __global__ void __launch_bounds__(Bounds2<P>::kThreads, 1) adj_f32x2_kernel(
   }
 }
 
+// ---------------------------------------------------------------- one-CTA sweeps, factored stencils
+//
+// With P_j = c2 + c1 u_j and M_j = c2 - c1 u_j (c1 = 1/(2 dx), c2 = nu/dx^2) the
+// semi-discrete Burgers right-hand side, its Jacobian F = f'(u) and F^T are
+//   f_j       = M_j (u_{j+1} - u_j) - P_j (u_j - u_{j-1})
+//   (F d)_j   = M_j (d_{j+1} - d_j) - P_j (d_j - d_{j-1}) - (P_{j+1} - P_{j-1}) d_j
+//   (F^T k)_j = P_{j+1} (k_{j+1} - k_j) - M_{j-1} (k_j - k_{j-1})
+// (from F_{j,j+1} = M_j, F_{j,j-1} = P_j, F_{jj} = -(P_{j+1} + M_{j-1})). The
+// kernels below evaluate these factored forms, with nM = -M = c1 u - c2 so that
+// every operation is one packed FMA or multiply: per point and RK4 step 51 packed
+// operations for the TLM and 45 for the ADJ (its base-state recomputation
+// included), against 61 and 74 for the expanded stencils.
+//
+// One CTA sweeps one direction over the whole window; thread t owns P contiguous
+// folded pairs. Every stage publishes the new values of each thread's first and
+// last pair (warp shuffles inside a warp, two shared slots per warp across warps)
+// before the thread computes its interior pairs, so the exchange and the
+// barrier that follows overlap with that work.
+
+struct Slots {  // [parity 2][array 2][side 2: first / last pair][32 warps]
+  f2* base;
+  __device__ __forceinline__ f2* at(int par, int a, int side, int w) const {
+    return base + ((par * 2 + a) * 2 + side) * 32 + w;
+  }
+};
+
+// Writes my first / last pair of array a to the warp-edge slots (lanes 0 / 31).
+// The ring ends are swapped by the writer: warp 0's first pair is the right
+// neighbour of the last warp's last pair as swap(.), and vice versa.
+__device__ __forceinline__ void put_edges(const Slots& S, int par, int a, int lane, int w, int nw, f2 first,
+                                          f2 last) {
+  const f2 fw = (w == 0) ? swp(first) : first;
+  const f2 lw = (w == nw - 1) ? swp(last) : last;
+  if (lane == 0) *S.at(par, a, 0, w) = fw;
+  if (lane == 31) *S.at(par, a, 1, w) = lw;
+}
+
+// After the barrier: the warp-edge lanes replace their shuffled halos by the slots.
+__device__ __forceinline__ void get_edges(const Slots& S, int par, int a, int lane, int wl, int wr, f2& left,
+                                          f2& right) {
+  const f2 sl = *S.at(par, a, 1, wl);
+  const f2 sr = *S.at(par, a, 0, wr);
+  left = (lane == 0) ? sl : left;
+  right = (lane == 31) ? sr : right;
+}
+
+// Neighbour pairs of my first and last pair in a chunk-major row (ring wrap and swap).
+template <int P>
+struct RowHalo {
+  int el, er;
+  bool swl, swr;
+  __device__ RowHalo(int tid, int NT) {
+    el = PRows<P>::elem(tid > 0 ? tid - 1 : NT - 1, P - 1, NT);
+    er = PRows<P>::elem(tid < NT - 1 ? tid + 1 : 0, 0, NT);
+    swl = tid == 0;
+    swr = tid == NT - 1;
+  }
+  __device__ __forceinline__ void get(const f2* row, f2& left, f2& right) const {
+    const f2 a = row[el], b = row[er];
+    left = swl ? swp(a) : a;
+    right = swr ? swp(b) : b;
+  }
+};
+
+template <int P>
+__global__ void __launch_bounds__(512, 1) tlm1_kernel(Geo g, const float* __restrict__ traj,
+                                                      const float* __restrict__ U0, int ldu,
+                                                      float* __restrict__ W, int ldw) {
+  static_assert(P >= 2 && P % 2 == 0, "pairs per thread");
+  using R = PRows<P>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  f2* sm = reinterpret_cast<f2*>(smraw);
+  const int H = g.H, NT = blockDim.x, tid = threadIdx.x;
+  const int lane = tid & 31, w = tid >> 5, nw = NT >> 5;
+  const int wl = (w + nw - 1) % nw, wr = (w + 1) % nw;
+  f2* xbuf[2] = {sm, sm + H};
+  f2* stage = sm + 2 * H;
+  const Slots S{stage + H};
+  const RowHalo<P> rh(tid, NT);
+  const int col = blockIdx.x;
+  const int i0 = tid * P;
+  const f2* trajp = reinterpret_cast<const f2*>(traj);
+  const f2 c1 = mk(g.c1), c2 = mk(g.c2), nc2 = mk(-g.c2), m1 = mk(-1.f), mh = mk(-g.h);
+  constexpr float kA[3] = {0.5f, 0.5f, 1.0f};
+  constexpr float kB[4] = {1.0f / 6.0f, 1.0f / 3.0f, 1.0f / 3.0f, 1.0f / 6.0f};
+  f2 dx[P], acc[P], dL, dR;
+  {
+    const float* u0 = U0 + (size_t)col * ldu;
+#pragma unroll
+    for (int p = 0; p < P; ++p) dx[p] = make_float2(u0[i0 + p], u0[H + i0 + p]);
+    const int il = rh.swl ? H - 1 : i0 - 1, ir = rh.swr ? 0 : i0 + P;
+    const f2 a = make_float2(u0[il], u0[H + il]), b = make_float2(u0[ir], u0[H + ir]);
+    dL = rh.swl ? swp(a) : a;
+    dR = rh.swr ? swp(b) : b;
+  }
+  float* wcol = W + (size_t)col * ldw;
+  if (g.N > 0) {
+    R::prefetch(xbuf[0], trajp + i0, tid, NT);
+    R::wait();
+  }
+  __syncthreads();
+  for (int t = 0;; ++t) {
+    const int oi = g.obs_of_step[t];
+    if (oi >= 0) {
+      R::store(stage, tid, NT, dx);
+      __syncthreads();
+      for (int o = tid; o < g.n_o; o += NT) {
+        int il, half;
+        if (pair_of(g.obs_idx[oi * g.n_o + o], g, 0, il, half)) {
+          const f2 v = stage[R::elem(il / P, il % P, NT)];
+          wcol[oi * g.n_o + o] = (half ? v.y : v.x) * g.inv_sigma;
+        }
+      }
+    }
+    if (t == g.N) break;
+    const f2* xb = xbuf[t & 1];
+    f2 x[P], U[P], D[P], uL, uR;
+    R::load(xb, tid, NT, x);
+    rh.get(xb, uL, uR);
+    if (t + 1 < g.N) R::prefetch(xbuf[(t + 1) & 1], trajp + (size_t)(t + 1) * H + i0, tid, NT);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      U[p] = x[p];
+      D[p] = dx[p];
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int par = s & 1;
+      const f2 bs = mk(kB[s]);
+      const f2 mha = mk(s < 3 ? -g.h * kA[s] : 0.f);
+      // P at pairs -1 .. P (halos included), forward differences of U and D
+      f2 Pv[P + 2], du[P + 1], dd[P + 1];
+      Pv[0] = fma2(c1, uL, c2);
+      Pv[P + 1] = fma2(c1, uR, c2);
+#pragma unroll
+      for (int p = 0; p < P; ++p) Pv[p + 1] = fma2(c1, U[p], c2);
+#pragma unroll
+      for (int q = 0; q <= P; ++q) {
+        const f2 dn = q < P ? D[q] : dR, dp = q > 0 ? D[q - 1] : dL;
+        dd[q] = fma2(dp, m1, dn);
+        if (s < 3) {
+          const f2 un = q < P ? U[q] : uR, up = q > 0 ? U[q - 1] : uL;
+          du[q] = fma2(up, m1, un);
+        }
+      }
+      f2 Un[P], Dn[P];
+      auto pair = [&](int p) {
+        const f2 nM = fma2(c1, U[p], nc2);
+        const f2 E = fma2(Pv[p], m1, Pv[p + 2]);
+        const f2 G = fma2(E, D[p], fma2(Pv[p + 1], dd[p], mul2(nM, dd[p + 1])));  // -(F D)_p
+        acc[p] = (s == 0) ? mul2(bs, G) : fma2(bs, G, acc[p]);
+        if (s < 3) {
+          const f2 gu = fma2(Pv[p + 1], du[p], mul2(nM, du[p + 1]));              // -f(U)_p
+          Un[p] = fma2(mha, gu, x[p]);
+          Dn[p] = fma2(mha, G, dx[p]);
+        } else {
+          dx[p] = fma2(mh, acc[p], dx[p]);
+        }
+      };
+      pair(0);
+      pair(P - 1);
+      f2 aL, aR, bL, bR;
+      if (s < 3) {
+        put_edges(S, par, 0, lane, w, nw, Un[0], Un[P - 1]);
+        put_edges(S, par, 1, lane, w, nw, Dn[0], Dn[P - 1]);
+        aL = shfl_up2(Un[P - 1]);
+        aR = shfl_dn2(Un[0]);
+        bL = shfl_up2(Dn[P - 1]);
+        bR = shfl_dn2(Dn[0]);
+      } else {
+        put_edges(S, par, 1, lane, w, nw, dx[0], dx[P - 1]);
+        bL = shfl_up2(dx[P - 1]);
+        bR = shfl_dn2(dx[0]);
+      }
+#pragma unroll
+      for (int p = 1; p < P - 1; ++p) pair(p);
+      if (s == 3) R::wait();
+      __syncthreads();
+      if (s < 3) {
+        get_edges(S, par, 0, lane, wl, wr, aL, aR);
+        get_edges(S, par, 1, lane, wl, wr, bL, bR);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          U[p] = Un[p];
+          D[p] = Dn[p];
+        }
+        uL = aL;
+        uR = aR;
+        dL = bL;
+        dR = bR;
+      } else {
+        get_edges(S, par, 1, lane, wl, wr, bL, bR);
+        dL = bL;
+        dR = bR;
+      }
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(512, 1) adj1_kernel(Geo g, const float* __restrict__ traj,
+                                                      const float* __restrict__ Win, int ldw,
+                                                      float* __restrict__ Out, int ldo) {
+  static_assert(P >= 2 && P % 2 == 0, "pairs per thread");
+  using R = PRows<P>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  f2* sm = reinterpret_cast<f2*>(smraw);
+  const int H = g.H, NT = blockDim.x, tid = threadIdx.x;
+  const int lane = tid & 31, w = tid >> 5, nw = NT >> 5;
+  const int wl = (w + nw - 1) % nw, wr = (w + 1) % nw;
+  f2* xbuf[2] = {sm, sm + H};
+  f2* ubuf[2] = {sm + 2 * H, sm + 3 * H};  // stage states 1, 2 of the step (also the obs staging row)
+  const Slots S{sm + 4 * H};
+  const RowHalo<P> rh(tid, NT);
+  const int col = blockIdx.x;
+  const int i0 = tid * P;
+  const f2* trajp = reinterpret_cast<const f2*>(traj);
+  const float* win = Win + (size_t)col * ldw;
+  const f2 c1 = mk(g.c1), c2 = mk(g.c2), nc2 = mk(-g.c2), m1 = mk(-1.f);
+  const f2 h3 = mk(g.h / 3.f), half = mk(0.5f);
+  constexpr float kA[3] = {0.5f, 0.5f, 1.0f};
+  f2 lam[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) lam[p] = mk(0.f);
+  if (g.N > 0) {
+    R::prefetch(xbuf[(g.N - 1) & 1], trajp + (size_t)(g.N - 1) * H + i0, tid, NT);
+    R::wait();
+  }
+  __syncthreads();
+  for (int t = g.N; t >= 1; --t) {
+    const int oi = g.obs_of_step[t];
+    if (oi >= 0) {
+      R::store(ubuf[0], tid, NT, lam);
+      __syncthreads();
+      for (int o = tid; o < g.n_o; o += NT) {
+        int il, half_;
+        if (pair_of(g.obs_idx[oi * g.n_o + o], g, 0, il, half_)) {
+          f2* cell = &ubuf[0][R::elem(il / P, il % P, NT)];
+          atomicAdd(half_ ? &cell->y : &cell->x, win[oi * g.n_o + o] * g.inv_sigma);
+        }
+      }
+      __syncthreads();
+      R::load(ubuf[0], tid, NT, lam);
+    }
+    const int r = t - 1;  // base state x_{t-1}
+    const f2* xb = xbuf[r & 1];
+    f2 x[P], U[P], uL, uR, kL, kR;
+    R::load(xb, tid, NT, x);
+    rh.get(xb, uL, uR);
+#pragma unroll
+    for (int p = 0; p < P; ++p) U[p] = x[p];
+    // forward: stage states U1, U2 (kept in shared memory) and U3 (registers)
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int par = s & 1;
+      const float ha = g.h * kA[s];
+      const f2 sc1 = mk(-ha * g.c1), sc2 = mk(ha * g.c2), nsc2 = mk(-ha * g.c2);
+      f2 du[P + 1], Un[P];
+#pragma unroll
+      for (int q = 0; q <= P; ++q) {
+        const f2 un = q < P ? U[q] : uR, up = q > 0 ? U[q - 1] : uL;
+        du[q] = fma2(up, m1, un);
+      }
+      auto pair = [&](int p) {
+        const f2 Ps = fma2(sc1, U[p], nsc2);   // -h a P
+        const f2 Ms = fma2(sc1, U[p], sc2);    // -h a nM
+        Un[p] = fma2(Ms, du[p + 1], fma2(Ps, du[p], x[p]));
+      };
+      pair(0);
+      pair(P - 1);
+      put_edges(S, par, 0, lane, w, nw, Un[0], Un[P - 1]);
+      f2 aL = shfl_up2(Un[P - 1]), aR = shfl_dn2(Un[0]);
+      if (s == 2) {  // kappa_3 = h/6 lambda' of my edge pairs
+        const f2 k0 = mul2(half, mul2(h3, lam[0])), kP = mul2(half, mul2(h3, lam[P - 1]));
+        put_edges(S, par, 1, lane, w, nw, k0, kP);
+        kL = shfl_up2(kP);
+        kR = shfl_dn2(k0);
+      }
+#pragma unroll
+      for (int p = 1; p < P - 1; ++p) pair(p);
+      if (s < 2) R::store(ubuf[s], tid, NT, Un);
+      __syncthreads();
+      if (s == 0 && r >= 1) R::prefetch(xbuf[(r - 1) & 1], trajp + (size_t)(r - 1) * H + i0, tid, NT);
+      get_edges(S, par, 0, lane, wl, wr, aL, aR);
+      if (s == 2) get_edges(S, par, 1, lane, wl, wr, kL, kR);
+      uL = aL;
+      uR = aR;
+#pragma unroll
+      for (int p = 0; p < P; ++p) U[p] = Un[p];
+    }
+    // backward: kappa_3 = h b_3 lambda', theta_s = F_s^T kappa_s, lambda += theta_s,
+    // kappa_{s-1} = h b_{s-1} lambda' + h a_{s-1} theta_s
+    f2 L3[P], K[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      L3[p] = mul2(h3, lam[p]);
+      K[p] = mul2(half, L3[p]);
+    }
+#pragma unroll
+    for (int s = 3; s >= 0; --s) {
+      const int par = s & 1;  // exchanges 3, 4, 5 of the step alternate with 2
+      if (s == 1 || s == 2) {
+        R::load(ubuf[s - 1], tid, NT, U);
+        rh.get(ubuf[s - 1], uL, uR);
+      } else if (s == 0) {
+        R::load(xb, tid, NT, U);
+        rh.get(xb, uL, uR);
+      }
+      f2 dk[P + 1], Kn[P];
+#pragma unroll
+      for (int q = 0; q <= P; ++q) {
+        const f2 kn = q < P ? K[q] : kR, kp = q > 0 ? K[q - 1] : kL;
+        dk[q] = fma2(kp, m1, kn);
+      }
+      const f2 hA = mk(s > 0 ? g.h * kA[s - 1] : 0.f);
+      auto pair = [&](int p) {
+        const f2 Pn = fma2(c1, p + 1 < P ? U[p + 1] : uR, c2);   // P_{p+1}
+        const f2 nMp = fma2(c1, p > 0 ? U[p - 1] : uL, nc2);     // nM_{p-1}
+        const f2 th = fma2(Pn, dk[p + 1], mul2(nMp, dk[p]));
+        lam[p] = add2(lam[p], th);
+        if (s == 3 || s == 2) Kn[p] = fma2(hA, th, L3[p]);
+        else if (s == 1) Kn[p] = fma2(hA, th, mul2(half, L3[p]));
+      };
+      pair(0);
+      pair(P - 1);
+      if (s > 0) {
+        put_edges(S, par, 1, lane, w, nw, Kn[0], Kn[P - 1]);
+        kL = shfl_up2(Kn[P - 1]);
+        kR = shfl_dn2(Kn[0]);
+      }
+#pragma unroll
+      for (int p = 1; p < P - 1; ++p) pair(p);
+      if (s > 0) {
+        if (s == 1) R::wait();
+        __syncthreads();
+        get_edges(S, par, 1, lane, wl, wr, kL, kR);
+#pragma unroll
+        for (int p = 0; p < P; ++p) K[p] = Kn[p];
+      }
+    }
+  }
+  float* out = Out + (size_t)col * ldo;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    out[i0 + p] = lam[p].x;
+    out[H + i0 + p] = lam[p].y;
+  }
+}
+
 // ---------------------------------------------------------------- host
 const size_t kMaxSmem2 = 227 * 1024;
 
@@ -535,6 +884,15 @@ int burgers_tlm_f32x2(const ModelGeom& m, const float* traj_folded, const float*
   int cl = cluster_for(H, k, 3);
   Geo g = make_geo(m, cl);
   int P = pairs_per_thread(g.Hs, m.pairs_tuned), NT = g.Hs / P;
+  if (cl == 1 && P >= 2 && NT <= 512) {
+    const size_t sm1 = (size_t)(3 * H + 256) * sizeof(f2);
+    switch (P) {
+      case 2: SC4_TRY(launch2(tlm1_kernel<2>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw)); break;
+      case 4: SC4_TRY(launch2(tlm1_kernel<4>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw)); break;
+      default: SC4_TRY(launch2(tlm1_kernel<8>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw)); break;
+    }
+    return SC4DVAR_OK;
+  }
   size_t smem = (size_t)(2 * g.Hs + g.Hs + 2 * kPad2 + 8 * 32) * sizeof(f2);
   if (cl > 1) {
     SC4_DISPATCH_PAIRS(P, SC4_TRY(launch2(tlm_f32x2_kernel<PP, true>, k * cl, NT, smem, cl, st, g,
@@ -553,6 +911,15 @@ int burgers_adj_f32x2(const ModelGeom& m, const float* traj_folded, const float*
   int cl = cluster_for(H, k, 4);
   Geo g = make_geo(m, cl);
   int P = pairs_per_thread(g.Hs, m.pairs_tuned), NT = g.Hs / P;
+  if (cl == 1 && P >= 2 && NT <= 512) {
+    const size_t sm1 = (size_t)(4 * H + 256) * sizeof(f2);
+    switch (P) {
+      case 2: SC4_TRY(launch2(adj1_kernel<2>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo)); break;
+      case 4: SC4_TRY(launch2(adj1_kernel<4>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo)); break;
+      default: SC4_TRY(launch2(adj1_kernel<8>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo)); break;
+    }
+    return SC4DVAR_OK;
+  }
   size_t smem = (size_t)(4 * (g.Hs + 2 * kPad2) + 4 * 32) * sizeof(f2);
   if (cl > 1) {
     SC4_DISPATCH_PAIRS(P, SC4_TRY(launch2(adj_f32x2_kernel<PP, true>, k * cl, NT, smem, cl, st, g,
