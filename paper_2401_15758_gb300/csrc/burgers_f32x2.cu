@@ -453,42 +453,34 @@ __global__ void __launch_bounds__(Bounds2<P>::kThreads, 1) adj_f32x2_kernel(
 //   (F^T k)_j = P_{j+1} (k_{j+1} - k_j) - M_{j-1} (k_j - k_{j-1})
 // (from F_{j,j+1} = M_j, F_{j,j-1} = P_j, F_{jj} = -(P_{j+1} + M_{j-1})). The
 // kernels below evaluate these factored forms, with nM = -M = c1 u - c2 so that
-// every operation is one packed FMA or multiply: per point and RK4 step 51 packed
-// operations for the TLM and 45 for the ADJ (its base-state recomputation
-// included), against 61 and 74 for the expanded stencils.
+// every operation is one packed FMA or multiply: per point and RK4 step about 51
+// packed operations for the TLM and 47 for the ADJ (its base-state
+// recomputation included), against 61 and 74 for the expanded stencils.
 //
 // One CTA sweeps one direction over the whole window; thread t owns P contiguous
-// folded pairs. Every stage publishes the new values of each thread's first and
-// last pair (warp shuffles inside a warp, two shared slots per warp across warps)
-// before the thread computes its interior pairs, so the exchange and the
-// barrier that follows overlap with that work.
+// folded pairs. In every stage a thread first computes its interior pairs, whose
+// neighbours it holds, then its first and last pair with the halos loaded after
+// the previous barrier, and stores those two results in the exchange rows (one
+// entry per thread, so stores and loads are unconditional and conflict-free)
+// before the barrier.
 
-struct Slots {  // [parity 2][array 2][side 2: first / last pair][32 warps]
-  f2* base;
-  __device__ __forceinline__ f2* at(int par, int a, int side, int w) const {
-    return base + ((par * 2 + a) * 2 + side) * 32 + w;
+// Exchange rows: [parity 2][array 2][NT] first pairs, then the same for last pairs.
+struct Xch {
+  f2* first;
+  f2* last;
+  int NT, tid, tl, tr;
+  bool swl, swr;
+  __device__ __forceinline__ void put(int par, int a, f2 f, f2 l) const {
+    first[(par * 2 + a) * NT + tid] = f;
+    last[(par * 2 + a) * NT + tid] = l;
+  }
+  // left neighbour of my first pair, right neighbour of my last pair (ring ends swapped)
+  __device__ __forceinline__ void get(int par, int a, f2& left, f2& right) const {
+    const f2 l = last[(par * 2 + a) * NT + tl], r = first[(par * 2 + a) * NT + tr];
+    left = swl ? swp(l) : l;
+    right = swr ? swp(r) : r;
   }
 };
-
-// Writes my first / last pair of array a to the warp-edge slots (lanes 0 / 31).
-// The ring ends are swapped by the writer: warp 0's first pair is the right
-// neighbour of the last warp's last pair as swap(.), and vice versa.
-__device__ __forceinline__ void put_edges(const Slots& S, int par, int a, int lane, int w, int nw, f2 first,
-                                          f2 last) {
-  const f2 fw = (w == 0) ? swp(first) : first;
-  const f2 lw = (w == nw - 1) ? swp(last) : last;
-  if (lane == 0) *S.at(par, a, 0, w) = fw;
-  if (lane == 31) *S.at(par, a, 1, w) = lw;
-}
-
-// After the barrier: the warp-edge lanes replace their shuffled halos by the slots.
-__device__ __forceinline__ void get_edges(const Slots& S, int par, int a, int lane, int wl, int wr, f2& left,
-                                          f2& right) {
-  const f2 sl = *S.at(par, a, 1, wl);
-  const f2 sr = *S.at(par, a, 0, wr);
-  left = (lane == 0) ? sl : left;
-  right = (lane == 31) ? sr : right;
-}
 
 // Neighbour pairs of my first and last pair in a chunk-major row (ring wrap and swap).
 template <int P>
@@ -509,19 +501,29 @@ struct RowHalo {
 };
 
 template <int P>
-__global__ void __launch_bounds__(512, 1) tlm1_kernel(Geo g, const float* __restrict__ traj,
-                                                      const float* __restrict__ U0, int ldu,
-                                                      float* __restrict__ W, int ldw) {
-  static_assert(P >= 2 && P % 2 == 0, "pairs per thread");
+struct Bounds1 {
+  static constexpr int kThreads = P >= 16 ? 256 : 512;
+};
+
+template <int P>
+__global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) tlm1_kernel(
+    Geo g, const float* __restrict__ traj, const float* __restrict__ U0, int ldu,
+    float* __restrict__ W, int ldw) {
+  static_assert(P >= 4 && P % 2 == 0, "pairs per thread");
   using R = PRows<P>;
   extern __shared__ __align__(16) unsigned char smraw[];
   f2* sm = reinterpret_cast<f2*>(smraw);
   const int H = g.H, NT = blockDim.x, tid = threadIdx.x;
-  const int lane = tid & 31, w = tid >> 5, nw = NT >> 5;
-  const int wl = (w + nw - 1) % nw, wr = (w + 1) % nw;
-  f2* xbuf[2] = {sm, sm + H};
-  f2* stage = sm + 2 * H;
-  const Slots S{stage + H};
+  f2* stage = sm + 2 * H;  // rows t (even / odd) at sm and sm + H
+  Xch X;
+  X.first = stage + H;
+  X.last = X.first + 4 * NT;
+  X.NT = NT;
+  X.tid = tid;
+  X.tl = tid > 0 ? tid - 1 : NT - 1;
+  X.tr = tid < NT - 1 ? tid + 1 : 0;
+  X.swl = tid == 0;
+  X.swr = tid == NT - 1;
   const RowHalo<P> rh(tid, NT);
   const int col = blockIdx.x;
   const int i0 = tid * P;
@@ -534,19 +536,21 @@ __global__ void __launch_bounds__(512, 1) tlm1_kernel(Geo g, const float* __rest
     const float* u0 = U0 + (size_t)col * ldu;
 #pragma unroll
     for (int p = 0; p < P; ++p) dx[p] = make_float2(u0[i0 + p], u0[H + i0 + p]);
-    const int il = rh.swl ? H - 1 : i0 - 1, ir = rh.swr ? 0 : i0 + P;
+    const int il = X.swl ? H - 1 : i0 - 1, ir = X.swr ? 0 : i0 + P;
     const f2 a = make_float2(u0[il], u0[H + il]), b = make_float2(u0[ir], u0[H + ir]);
-    dL = rh.swl ? swp(a) : a;
-    dR = rh.swr ? swp(b) : b;
+    dL = X.swl ? swp(a) : a;
+    dR = X.swr ? swp(b) : b;
   }
   float* wcol = W + (size_t)col * ldw;
   if (g.N > 0) {
-    R::prefetch(xbuf[0], trajp + i0, tid, NT);
+    R::prefetch(sm, trajp + i0, tid, NT);
     R::wait();
   }
   __syncthreads();
+  int oi_next = g.obs_of_step[0];
   for (int t = 0;; ++t) {
-    const int oi = g.obs_of_step[t];
+    const int oi = oi_next;
+    if (t < g.N) oi_next = g.obs_of_step[t + 1];
     if (oi >= 0) {
       R::store(stage, tid, NT, dx);
       __syncthreads();
@@ -559,11 +563,11 @@ __global__ void __launch_bounds__(512, 1) tlm1_kernel(Geo g, const float* __rest
       }
     }
     if (t == g.N) break;
-    const f2* xb = xbuf[t & 1];
+    const f2* xb = sm + (t & 1) * H;
     f2 x[P], U[P], D[P], uL, uR;
     R::load(xb, tid, NT, x);
     rh.get(xb, uL, uR);
-    if (t + 1 < g.N) R::prefetch(xbuf[(t + 1) & 1], trajp + (size_t)(t + 1) * H + i0, tid, NT);
+    if (t + 1 < g.N) R::prefetch(sm + ((t + 1) & 1) * H, trajp + (size_t)(t + 1) * H + i0, tid, NT);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       U[p] = x[p];
@@ -571,92 +575,85 @@ __global__ void __launch_bounds__(512, 1) tlm1_kernel(Geo g, const float* __rest
     }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      const int par = s & 1;
       const f2 bs = mk(kB[s]);
       const f2 mha = mk(s < 3 ? -g.h * kA[s] : 0.f);
-      // P at pairs -1 .. P (halos included), forward differences of U and D
-      f2 Pv[P + 2], du[P + 1], dd[P + 1];
-      Pv[0] = fma2(c1, uL, c2);
-      Pv[P + 1] = fma2(c1, uR, c2);
-#pragma unroll
-      for (int p = 0; p < P; ++p) Pv[p + 1] = fma2(c1, U[p], c2);
-#pragma unroll
-      for (int q = 0; q <= P; ++q) {
-        const f2 dn = q < P ? D[q] : dR, dp = q > 0 ? D[q - 1] : dL;
-        dd[q] = fma2(dp, m1, dn);
-        if (s < 3) {
-          const f2 un = q < P ? U[q] : uR, up = q > 0 ? U[q - 1] : uL;
-          du[q] = fma2(up, m1, un);
-        }
-      }
       f2 Un[P], Dn[P];
-      auto pair = [&](int p) {
+      // pair p from P at p-1, p, p+1 and the forward differences at p (q = p) and p + 1
+      auto pair = [&](int p, f2 Pm, f2 Pc, f2 Pn, f2 du0, f2 du1, f2 dd0, f2 dd1) {
         const f2 nM = fma2(c1, U[p], nc2);
-        const f2 E = fma2(Pv[p], m1, Pv[p + 2]);
-        const f2 G = fma2(E, D[p], fma2(Pv[p + 1], dd[p], mul2(nM, dd[p + 1])));  // -(F D)_p
+        const f2 E = fma2(Pm, m1, Pn);
+        const f2 G = fma2(E, D[p], fma2(Pc, dd0, mul2(nM, dd1)));  // -(F D)_p
         acc[p] = (s == 0) ? mul2(bs, G) : fma2(bs, G, acc[p]);
         if (s < 3) {
-          const f2 gu = fma2(Pv[p + 1], du[p], mul2(nM, du[p + 1]));              // -f(U)_p
+          const f2 gu = fma2(Pc, du0, mul2(nM, du1));               // -f(U)_p
           Un[p] = fma2(mha, gu, x[p]);
           Dn[p] = fma2(mha, G, dx[p]);
         } else {
           dx[p] = fma2(mh, acc[p], dx[p]);
         }
       };
-      pair(0);
-      pair(P - 1);
-      f2 aL, aR, bL, bR;
-      if (s < 3) {
-        put_edges(S, par, 0, lane, w, nw, Un[0], Un[P - 1]);
-        put_edges(S, par, 1, lane, w, nw, Dn[0], Dn[P - 1]);
-        aL = shfl_up2(Un[P - 1]);
-        aR = shfl_dn2(Un[0]);
-        bL = shfl_up2(Dn[P - 1]);
-        bR = shfl_dn2(Dn[0]);
-      } else {
-        put_edges(S, par, 1, lane, w, nw, dx[0], dx[P - 1]);
-        bL = shfl_up2(dx[P - 1]);
-        bR = shfl_dn2(dx[0]);
-      }
+      // interior pairs 1 .. P-2, streaming a window of P and differences
+      const f2 P0 = fma2(c1, U[0], c2), P1 = fma2(c1, U[1], c2);
+      const f2 du1 = fma2(U[0], m1, U[1]), dd1 = fma2(D[0], m1, D[1]);
+      f2 Pm = P0, Pc = P1, dum = du1, ddm = dd1;
 #pragma unroll
-      for (int p = 1; p < P - 1; ++p) pair(p);
-      if (s == 3) R::wait();
+      for (int p = 1; p < P - 1; ++p) {
+        const f2 Pn = fma2(c1, U[p + 1], c2);
+        const f2 dun = fma2(U[p], m1, U[p + 1]), ddn = fma2(D[p], m1, D[p + 1]);
+        pair(p, Pm, Pc, Pn, dum, dun, ddm, ddn);
+        Pm = Pc;
+        Pc = Pn;
+        dum = dun;
+        ddm = ddn;
+      }
+      // last and first pair with the halos
+      pair(P - 1, Pm, Pc, fma2(c1, uR, c2), dum, fma2(U[P - 1], m1, uR), ddm, fma2(D[P - 1], m1, dR));
+      pair(0, fma2(c1, uL, c2), P0, P1, fma2(uL, m1, U[0]), du1, fma2(dL, m1, D[0]), dd1);
+      const int par = s & 1;
+      if (s < 3) {
+        X.put(par, 0, Un[0], Un[P - 1]);
+        X.put(par, 1, Dn[0], Dn[P - 1]);
+      } else {
+        X.put(par, 1, dx[0], dx[P - 1]);
+        R::wait();
+      }
       __syncthreads();
       if (s < 3) {
-        get_edges(S, par, 0, lane, wl, wr, aL, aR);
-        get_edges(S, par, 1, lane, wl, wr, bL, bR);
+        X.get(par, 0, uL, uR);
+        X.get(par, 1, dL, dR);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           U[p] = Un[p];
           D[p] = Dn[p];
         }
-        uL = aL;
-        uR = aR;
-        dL = bL;
-        dR = bR;
       } else {
-        get_edges(S, par, 1, lane, wl, wr, bL, bR);
-        dL = bL;
-        dR = bR;
+        X.get(par, 1, dL, dR);
       }
     }
   }
 }
 
 template <int P>
-__global__ void __launch_bounds__(512, 1) adj1_kernel(Geo g, const float* __restrict__ traj,
-                                                      const float* __restrict__ Win, int ldw,
-                                                      float* __restrict__ Out, int ldo) {
-  static_assert(P >= 2 && P % 2 == 0, "pairs per thread");
+__global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) adj1_kernel(
+    Geo g, const float* __restrict__ traj, const float* __restrict__ Win, int ldw,
+    float* __restrict__ Out, int ldo) {
+  static_assert(P >= 4 && P % 2 == 0, "pairs per thread");
   using R = PRows<P>;
   extern __shared__ __align__(16) unsigned char smraw[];
   f2* sm = reinterpret_cast<f2*>(smraw);
   const int H = g.H, NT = blockDim.x, tid = threadIdx.x;
-  const int lane = tid & 31, w = tid >> 5, nw = NT >> 5;
-  const int wl = (w + nw - 1) % nw, wr = (w + 1) % nw;
-  f2* xbuf[2] = {sm, sm + H};
-  f2* ubuf[2] = {sm + 2 * H, sm + 3 * H};  // stage states 1, 2 of the step (also the obs staging row)
-  const Slots S{sm + 4 * H};
+  // rows x_r (even / odd r) at sm and sm + H; stage states 1, 2 of the step at
+  // ubuf[0], ubuf[1] (ubuf[0] also stages lambda for the observation forcing)
+  f2* ubuf[2] = {sm + 2 * H, sm + 3 * H};
+  Xch X;
+  X.first = sm + 4 * H;
+  X.last = X.first + 4 * NT;
+  X.NT = NT;
+  X.tid = tid;
+  X.tl = tid > 0 ? tid - 1 : NT - 1;
+  X.tr = tid < NT - 1 ? tid + 1 : 0;
+  X.swl = tid == 0;
+  X.swr = tid == NT - 1;
   const RowHalo<P> rh(tid, NT);
   const int col = blockIdx.x;
   const int i0 = tid * P;
@@ -669,12 +666,14 @@ __global__ void __launch_bounds__(512, 1) adj1_kernel(Geo g, const float* __rest
 #pragma unroll
   for (int p = 0; p < P; ++p) lam[p] = mk(0.f);
   if (g.N > 0) {
-    R::prefetch(xbuf[(g.N - 1) & 1], trajp + (size_t)(g.N - 1) * H + i0, tid, NT);
+    R::prefetch(sm + ((g.N - 1) & 1) * H, trajp + (size_t)(g.N - 1) * H + i0, tid, NT);
     R::wait();
   }
   __syncthreads();
+  int oi_next = g.obs_of_step[g.N];
   for (int t = g.N; t >= 1; --t) {
-    const int oi = g.obs_of_step[t];
+    const int oi = oi_next;
+    oi_next = g.obs_of_step[t - 1];
     if (oi >= 0) {
       R::store(ubuf[0], tid, NT, lam);
       __syncthreads();
@@ -689,7 +688,7 @@ __global__ void __launch_bounds__(512, 1) adj1_kernel(Geo g, const float* __rest
       R::load(ubuf[0], tid, NT, lam);
     }
     const int r = t - 1;  // base state x_{t-1}
-    const f2* xb = xbuf[r & 1];
+    const f2* xb = sm + (r & 1) * H;
     f2 x[P], U[P], uL, uR, kL, kR;
     R::load(xb, tid, NT, x);
     rh.get(xb, uL, uR);
@@ -698,39 +697,34 @@ __global__ void __launch_bounds__(512, 1) adj1_kernel(Geo g, const float* __rest
     // forward: stage states U1, U2 (kept in shared memory) and U3 (registers)
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      const int par = s & 1;
       const float ha = g.h * kA[s];
       const f2 sc1 = mk(-ha * g.c1), sc2 = mk(ha * g.c2), nsc2 = mk(-ha * g.c2);
-      f2 du[P + 1], Un[P];
-#pragma unroll
-      for (int q = 0; q <= P; ++q) {
-        const f2 un = q < P ? U[q] : uR, up = q > 0 ? U[q - 1] : uL;
-        du[q] = fma2(up, m1, un);
-      }
-      auto pair = [&](int p) {
+      f2 Un[P];
+      // U_{s+1} = x - h a (nM du_{p+1} + P du_p) with du_q = U_q - U_{q-1}
+      auto pair = [&](int p, f2 du0, f2 du1) {
         const f2 Ps = fma2(sc1, U[p], nsc2);   // -h a P
         const f2 Ms = fma2(sc1, U[p], sc2);    // -h a nM
-        Un[p] = fma2(Ms, du[p + 1], fma2(Ps, du[p], x[p]));
+        Un[p] = fma2(Ms, du1, fma2(Ps, du0, x[p]));
       };
-      pair(0);
-      pair(P - 1);
-      put_edges(S, par, 0, lane, w, nw, Un[0], Un[P - 1]);
-      f2 aL = shfl_up2(Un[P - 1]), aR = shfl_dn2(Un[0]);
-      if (s == 2) {  // kappa_3 = h/6 lambda' of my edge pairs
-        const f2 k0 = mul2(half, mul2(h3, lam[0])), kP = mul2(half, mul2(h3, lam[P - 1]));
-        put_edges(S, par, 1, lane, w, nw, k0, kP);
-        kL = shfl_up2(kP);
-        kR = shfl_dn2(k0);
-      }
+      const f2 du1 = fma2(U[0], m1, U[1]);
+      f2 dum = du1;
 #pragma unroll
-      for (int p = 1; p < P - 1; ++p) pair(p);
+      for (int p = 1; p < P - 1; ++p) {
+        const f2 dun = fma2(U[p], m1, U[p + 1]);
+        pair(p, dum, dun);
+        dum = dun;
+      }
+      pair(P - 1, dum, fma2(U[P - 1], m1, uR));
+      pair(0, fma2(uL, m1, U[0]), du1);
+      const int par = s & 1;
+      X.put(par, 0, Un[0], Un[P - 1]);
+      if (s == 2)  // kappa_3 = h/6 lambda' of my edge pairs
+        X.put(par, 1, mul2(half, mul2(h3, lam[0])), mul2(half, mul2(h3, lam[P - 1])));
       if (s < 2) R::store(ubuf[s], tid, NT, Un);
       __syncthreads();
-      if (s == 0 && r >= 1) R::prefetch(xbuf[(r - 1) & 1], trajp + (size_t)(r - 1) * H + i0, tid, NT);
-      get_edges(S, par, 0, lane, wl, wr, aL, aR);
-      if (s == 2) get_edges(S, par, 1, lane, wl, wr, kL, kR);
-      uL = aL;
-      uR = aR;
+      if (s == 0 && r >= 1) R::prefetch(sm + ((r - 1) & 1) * H, trajp + (size_t)(r - 1) * H + i0, tid, NT);
+      X.get(par, 0, uL, uR);
+      if (s == 2) X.get(par, 1, kL, kR);
 #pragma unroll
       for (int p = 0; p < P; ++p) U[p] = Un[p];
     }
@@ -744,42 +738,40 @@ __global__ void __launch_bounds__(512, 1) adj1_kernel(Geo g, const float* __rest
     }
 #pragma unroll
     for (int s = 3; s >= 0; --s) {
-      const int par = s & 1;  // exchanges 3, 4, 5 of the step alternate with 2
-      if (s == 1 || s == 2) {
-        R::load(ubuf[s - 1], tid, NT, U);
-        rh.get(ubuf[s - 1], uL, uR);
-      } else if (s == 0) {
-        R::load(xb, tid, NT, U);
-        rh.get(xb, uL, uR);
-      }
-      f2 dk[P + 1], Kn[P];
-#pragma unroll
-      for (int q = 0; q <= P; ++q) {
-        const f2 kn = q < P ? K[q] : kR, kp = q > 0 ? K[q - 1] : kL;
-        dk[q] = fma2(kp, m1, kn);
-      }
+      if (s == 1 || s == 2) rh.get(ubuf[s - 1], uL, uR);
+      else if (s == 0) rh.get(xb, uL, uR);
       const f2 hA = mk(s > 0 ? g.h * kA[s - 1] : 0.f);
-      auto pair = [&](int p) {
-        const f2 Pn = fma2(c1, p + 1 < P ? U[p + 1] : uR, c2);   // P_{p+1}
-        const f2 nMp = fma2(c1, p > 0 ? U[p - 1] : uL, nc2);     // nM_{p-1}
-        const f2 th = fma2(Pn, dk[p + 1], mul2(nMp, dk[p]));
+      f2 Kn[P];
+      // theta_p = P_{p+1} dk_{p+1} + nM_{p-1} dk_p with dk_q = K_q - K_{q-1}
+      auto pair = [&](int p, f2 nMm, f2 Pn, f2 dk0, f2 dk1) {
+        const f2 th = fma2(Pn, dk1, mul2(nMm, dk0));
         lam[p] = add2(lam[p], th);
         if (s == 3 || s == 2) Kn[p] = fma2(hA, th, L3[p]);
         else if (s == 1) Kn[p] = fma2(hA, th, mul2(half, L3[p]));
       };
-      pair(0);
-      pair(P - 1);
-      if (s > 0) {
-        put_edges(S, par, 1, lane, w, nw, Kn[0], Kn[P - 1]);
-        kL = shfl_up2(Kn[P - 1]);
-        kR = shfl_dn2(Kn[0]);
-      }
+      const f2 nM0 = fma2(c1, U[0], nc2), dk1 = fma2(K[0], m1, K[1]);
+      f2 nMm = nM0, dkm = dk1;
 #pragma unroll
-      for (int p = 1; p < P - 1; ++p) pair(p);
+      for (int p = 1; p < P - 1; ++p) {
+        const f2 dkn = fma2(K[p], m1, K[p + 1]);
+        pair(p, nMm, fma2(c1, U[p + 1], c2), dkm, dkn);
+        nMm = fma2(c1, U[p], nc2);
+        dkm = dkn;
+      }
+      pair(P - 1, nMm, fma2(c1, uR, c2), dkm, fma2(K[P - 1], m1, kR));
+      pair(0, fma2(c1, uL, nc2), fma2(c1, U[1], c2), fma2(kL, m1, K[0]), dk1);
       if (s > 0) {
-        if (s == 1) R::wait();
+        const int par = s & 1;  // exchanges 3, 4, 5 of the step alternate with 2
+        X.put(par, 1, Kn[0], Kn[P - 1]);
+        // the next stage state (my own chunks) is loaded before the barrier
+        if (s == 1) {
+          R::load(xb, tid, NT, U);
+          R::wait();
+        } else {
+          R::load(ubuf[s - 2], tid, NT, U);
+        }
         __syncthreads();
-        get_edges(S, par, 1, lane, wl, wr, kL, kR);
+        X.get(par, 1, kL, kR);
 #pragma unroll
         for (int p = 0; p < P; ++p) K[p] = Kn[p];
       }
@@ -796,12 +788,17 @@ __global__ void __launch_bounds__(512, 1) adj1_kernel(Geo g, const float* __rest
 // ---------------------------------------------------------------- host
 const size_t kMaxSmem2 = 227 * 1024;
 
-int pairs_per_thread(int Hs, int tuned) {
+// Pairs per thread of a sweep over Hs pairs per CTA. Default: up to 8 (512
+// threads); the one-CTA adjoint sweep over 4096 pairs (n = 8192) takes 16 pairs
+// per thread (256 threads), which measured faster there.
+int pairs_per_thread(int Hs, int tuned, bool adj = false) {
   static int forced = [] {
     const char* e = getenv("SC4DVAR_PAIRS_P");
     return e ? atoi(e) : 0;
   }();
-  int P = tuned > 0 ? tuned : (forced > 0 ? forced : std::max(1, std::min(8, Hs / 512)));
+  const int dflt = (adj && Hs == 4096) ? 16 : std::max(1, std::min(8, Hs / 512));
+  int P = tuned > 0 ? tuned : (forced > 0 ? forced : dflt);
+  if (P == 16 && Hs % 16 == 0 && Hs / 16 >= 64 && Hs / 16 <= 256) return P;  // one-CTA sweeps only
   if (P != 1 && P != 2 && P != 4 && P != 8) P = 8;
   while (P > 1 && Hs / P < 32) P /= 2;
   while (Hs / P > Bounds2<8>::kThreads * (P >= 8 ? 1 : 2) && P < 8) P *= 2;
@@ -883,14 +880,14 @@ int burgers_tlm_f32x2(const ModelGeom& m, const float* traj_folded, const float*
   const int H = m.n / 2;
   int cl = cluster_for(H, k, 3);
   Geo g = make_geo(m, cl);
-  int P = pairs_per_thread(g.Hs, m.pairs_tuned), NT = g.Hs / P;
-  if (cl == 1 && P >= 2 && NT <= 512) {
-    const size_t sm1 = (size_t)(3 * H + 256) * sizeof(f2);
-    switch (P) {
-      case 2: SC4_TRY(launch2(tlm1_kernel<2>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw)); break;
-      case 4: SC4_TRY(launch2(tlm1_kernel<4>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw)); break;
-      default: SC4_TRY(launch2(tlm1_kernel<8>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw)); break;
-    }
+  int P = pairs_per_thread(g.Hs, m.pairs_tuned);
+  if (cl > 1 && P > 8) P = 8;
+  int NT = g.Hs / P;
+  if (cl == 1 && P >= 4 && NT <= 512) {
+    const size_t sm1 = (size_t)(3 * H + 8 * NT) * sizeof(f2);
+    if (P == 4) SC4_TRY(launch2(tlm1_kernel<4>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw));
+    else if (P == 16) SC4_TRY(launch2(tlm1_kernel<16>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw));
+    else SC4_TRY(launch2(tlm1_kernel<8>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw));
     return SC4DVAR_OK;
   }
   size_t smem = (size_t)(2 * g.Hs + g.Hs + 2 * kPad2 + 8 * 32) * sizeof(f2);
@@ -910,14 +907,14 @@ int burgers_adj_f32x2(const ModelGeom& m, const float* traj_folded, const float*
   const int H = m.n / 2;
   int cl = cluster_for(H, k, 4);
   Geo g = make_geo(m, cl);
-  int P = pairs_per_thread(g.Hs, m.pairs_tuned), NT = g.Hs / P;
-  if (cl == 1 && P >= 2 && NT <= 512) {
-    const size_t sm1 = (size_t)(4 * H + 256) * sizeof(f2);
-    switch (P) {
-      case 2: SC4_TRY(launch2(adj1_kernel<2>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo)); break;
-      case 4: SC4_TRY(launch2(adj1_kernel<4>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo)); break;
-      default: SC4_TRY(launch2(adj1_kernel<8>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo)); break;
-    }
+  int P = pairs_per_thread(g.Hs, m.pairs_tuned, true);
+  if (cl > 1 && P > 8) P = 8;
+  int NT = g.Hs / P;
+  if (cl == 1 && P >= 4 && NT <= 512) {
+    const size_t sm1 = (size_t)(4 * H + 8 * NT) * sizeof(f2);
+    if (P == 4) SC4_TRY(launch2(adj1_kernel<4>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo));
+    else if (P == 16) SC4_TRY(launch2(adj1_kernel<16>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo));
+    else SC4_TRY(launch2(adj1_kernel<8>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo));
     return SC4DVAR_OK;
   }
   size_t smem = (size_t)(4 * (g.Hs + 2 * kPad2) + 4 * 32) * sizeof(f2);
