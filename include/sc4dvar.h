@@ -46,7 +46,9 @@ extern "C" {
 #define SC4DVAR_ERR_NOT_SPD       -3   /* a Cholesky factorization failed        */
 #define SC4DVAR_ERR_BREAKDOWN     -4   /* PCG: p^T (I+H) p <= 0 or not finite     */
 #define SC4DVAR_ERR_NOT_CONVERGED -5   /* PCG: maxit reached above tolerance      */
-#define SC4DVAR_ERR_TIMEOUT       -6   /* a bounded device wait gave up           */
+#define SC4DVAR_ERR_TIMEOUT       -6   /* reserved for a bounded device wait that
+                                           gives up; no kernel of this version waits
+                                           on another, so no call returns it        */
 #define SC4DVAR_ERR_OOM           -7
 #define SC4DVAR_ERR_STATE         -8   /* e.g. no forward trajectory stored yet   */
 
@@ -219,6 +221,9 @@ typedef struct {
     int64_t tlm_online, adj_online;
     int64_t tlm_offline, adj_offline;
     int64_t tlm_kappa, adj_kappa;
+    int64_t qr_shifted;    /* CholeskyQR passes that failed and were redone with a
+                              diagonal shift (shifted CholeskyQR3, no counterpart in
+                              the paper, which takes Householder QR)               */
 } sc4dvar_counters_t;
 
 /* ---- library --------------------------------------------------------------- */
@@ -325,6 +330,8 @@ int sc4dvar_kappa_estimate(sc4dvar_problem_t p, sc4dvar_precond_t P, uint64_t se
  * (NULL = Prec_Gamma). FP64 vectors and reductions; the operator runs in
  * opts->prec. With FP32 and refine > 0 the iteration is restarted on the FP64
  * residual b - (I + H) x (defect correction) until that residual meets tol.
+ * info->status is SC4DVAR_ERR_BREAKDOWN when p^T (I + H) p is not positive or
+ * not finite, and at once (no iteration) when b has a non-finite entry.
  * Synchronizes; info may be NULL. */
 int sc4dvar_pcg(sc4dvar_problem_t p, sc4dvar_precond_t P, const double* b_dev, double* x_dev,
                 const sc4dvar_pcg_opts* opts, sc4dvar_pcg_info* info, void* stream);

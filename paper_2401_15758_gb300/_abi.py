@@ -91,7 +91,7 @@ class GnInfo(C.Structure):
 class Counters(C.Structure):
     _fields_ = [("fwd", C.c_int64), ("tlm_online", C.c_int64), ("adj_online", C.c_int64),
                 ("tlm_offline", C.c_int64), ("adj_offline", C.c_int64),
-                ("tlm_kappa", C.c_int64), ("adj_kappa", C.c_int64)]
+                ("tlm_kappa", C.c_int64), ("adj_kappa", C.c_int64), ("qr_shifted", C.c_int64)]
 
 
 P = C.c_void_p

@@ -405,6 +405,7 @@ static int host_scalar(Prob* P, double* out, cudaStream_t st) {
 // Workspace for the dense steps of one sketch.
 struct SketchWS {
   Buf a, b, c, g, g2, u, w, info, jw;
+  int64_t* shifted = nullptr;  // problem counter of shifted CholeskyQR retries
   void release() {
     a.release(); b.release(); c.release(); g.release(); g2.release(); u.release(); w.release();
     info.release(); jw.release();
@@ -450,6 +451,7 @@ static int cholqr_pass(int rows, int l, const T* src, int lds, T* dst, int ldd, 
     SC4_TRY(chol_lower(l, G, l, ws.info.as<int>(), st));
     s = check_info(ws.info, "shifted CholeskyQR", st);
     if (s == SC4DVAR_OK && shifted) *shifted = true;
+    if (s == SC4DVAR_OK && ws.shifted) ++*ws.shifted;
   }
   if (s != SC4DVAR_OK) return s;
   SC4_TRY(trtri_lower(l, G, l, Li, l, 0.0, st));
@@ -457,7 +459,12 @@ static int cholqr_pass(int rows, int l, const T* src, int lds, T* dst, int ldd, 
 }
 
 // Thin QR Y = Q R by CholeskyQR2 (Q separate from Y; a third pass when the
-// first one needed a shift: shifted CholeskyQR3).
+// first one needed a shift: shifted CholeskyQR3). When Y is rank deficient
+// (a sketch wider than the operator's numerical rank) the columns of the first
+// pass beyond that rank are tiny and the later Gram matrices are singular too:
+// every pass may then take the shift, those columns stay tiny (their A^T q is
+// negligible and the thin SVD that follows drops them) and the others come out
+// orthonormal.
 template <typename T>
 static int cholqr2(int rows, int l, const T* Y, int ldy, T* Q, int ldq, SketchWS& ws, cudaStream_t st) {
   bool shifted = false;
@@ -467,7 +474,7 @@ static int cholqr2(int rows, int l, const T* Y, int ldy, T* Q, int ldq, SketchWS
   int passes = shifted ? 2 : 1;
   for (int p = 0; p < passes; ++p) {
     SC4_TRY(copy_block<T, T>(rows, l, Q, ldq, C, rows, st));
-    SC4_TRY(cholqr_pass<T>(rows, l, C, rows, Q, ldq, false, nullptr, ws, st));
+    SC4_TRY(cholqr_pass<T>(rows, l, C, rows, Q, ldq, true, nullptr, ws, st));
   }
   return SC4DVAR_OK;
 }
@@ -623,6 +630,7 @@ static int build_randsvd(Prob* P, const sc4dvar_sketch_opts& o, const double* Om
   const uint64_t s_om = SC4DVAR_STREAM_SKETCH + (uint64_t)o.gn_iter;
   const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
   SketchWS ws;
+  ws.shifted = &P->counters.qr_shifted;
   Buf Om, Y, Qall, Wt, tmp;
   int rc = SC4DVAR_OK;
   auto body = [&]() -> int {
@@ -713,6 +721,7 @@ static int build_nystrom(Prob* P, const sc4dvar_sketch_opts& o, const double* Om
   const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
   const double eps = (sizeof(T) == 4) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
   SketchWS ws;
+  ws.shifted = &P->counters.qr_shifted;
   Buf Om, Y, Yc, tmp;
   auto body = [&]() -> int {
     SC4_TRY(Om.ensure((size_t)n * lmax * sizeof(T)));
@@ -861,6 +870,7 @@ static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double*
   const uint64_t s_ps = s_om + SC4DVAR_STREAM_PSI;
   const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
   SketchWS ws;
+  ws.shifted = &P->counters.qr_shifted;
   Buf Om, Ps, Y, QY, Z, Wt, tmp, Mq, Mr, Mb;
   const int ldq = l2max, ldr = lmax;  // Q_M (l2 x l1) and R_M (l1 x l1) at their largest
   auto body = [&]() -> int {
@@ -907,6 +917,7 @@ static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double*
         {
           // QR of the new block into Q_Y's next columns (cholqr2 needs its own c buffer)
           SketchWS ws2;
+          ws2.shifted = &P->counters.qr_shifted;
           int s2 = cholqr2<T>(m, lh1, yh, m, qy + (size_t)m * l1, m, ws2, st);
           cudaStreamSynchronize(st);
           ws2.release();
@@ -959,8 +970,16 @@ static int pcg_run(Prob* P, Prec* pc, const double* b, double* x, const sc4dvar_
   fill_kernel<<<div_up(n, 256), 256, 0, st>>>(n, 0.0, x);
   SC4_LAUNCH_CHECK();
   double relres = 0.0;
-  if (bnorm == 0.0) {
-    if (info) { info->iterations = 0; info->restarts = 0; info->relres = 0.0; info->status = 0; }
+  if (bnorm == 0.0 || !std::isfinite(bnorm)) {
+    // b = 0: x = 0 solves it; a non-finite b: a breakdown before the first iteration
+    const bool ok = bnorm == 0.0;
+    if (info) {
+      info->iterations = 0;
+      info->restarts = 0;
+      info->relres = ok ? 0.0 : bnorm;
+      info->status = ok ? SC4DVAR_OK : SC4DVAR_ERR_BREAKDOWN;
+    }
+    cudaStreamSynchronize(st);
     wb.release();
     return SC4DVAR_OK;
   }

@@ -94,3 +94,21 @@ def test_pcg_reports_not_converged():
     # CG minimises the energy norm of the error, so two steps may leave a
     # residual above |b|; it is finite and above the tolerance
     assert np.isfinite(info["relres"]) and info["relres"] > 1e-12 and torch.isfinite(x).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_pcg_nonfinite_rhs_is_a_breakdown(prec):
+    """A right-hand side with a NaN (made on the host) ends the solve at once
+    with status SC4DVAR_ERR_BREAKDOWN and no iterations; the handle stays
+    usable for the next, finite solve."""
+    import paper_2401_15758_gb300 as g
+    wl, prob = burgers_problem()
+    prob.fwd(torch.zeros(wl.n, dtype=torch.float64, device="cuda"))
+    p = g.FP64 if prec == "fp64" else g.FP32
+    b = np.random.default_rng(3).standard_normal(wl.n)
+    b[17] = np.nan
+    x, info = prob.pcg(torch.tensor(b, device="cuda"), None, tol=1e-6, prec=p)
+    assert info["status"] == g._abi.ERR_BREAKDOWN and info["iterations"] == 0
+    b[17] = 0.0
+    x, info = prob.pcg(torch.tensor(b, device="cuda"), None, tol=1e-6, prec=p)
+    assert info["status"] == OK and np.all(np.isfinite(x.cpu().numpy()))

@@ -44,17 +44,20 @@ def test_sketch_matches_oracle_given_omega(small, method, l):
         lr = sketch.singleview(ref.A, ref.At, Om, Ps)
     X = np.random.default_rng(1).standard_normal((wl.n, 4))
     ref_act = hhat_action(lr.V, lr.lam, X)
-    assert rel(hhat_action(V, lam, X), ref_act) <= 1e-8
+    assert rel(hhat_action(V, lam, X), ref_act) <= 1e-12
+    # eigenvalues: CholeskyQR2 + a Jacobi eigen-solve of the Gram matrix against
+    # Householder QR + SVD; both carry an absolute error of order u lambda_1 in
+    # every eigenvalue, so they are compared on the scale of lambda_1
     lam_ref = np.sort(lr.lam)[::-1]
     big = lam_ref > 1e-6 * lam_ref[0]
-    assert np.allclose(lam[:big.sum()], lam_ref[big], rtol=1e-8)
+    assert np.max(np.abs(lam[:big.sum()] - lam_ref[big])) <= 1e-10 * lam_ref[0]
     # V orthonormal
-    assert np.max(np.abs(V.T @ V - np.eye(V.shape[1]))) <= 1e-8
+    assert np.max(np.abs(V.T @ V - np.eye(V.shape[1]))) <= 1e-12
     # the Woodbury apply inverts I + H_hat
     R = np.random.default_rng(2).standard_normal((3, wl.n))
     Z = pc.apply(torch.tensor(R, device="cuda")).cpu().numpy()
     back = Z.T + hhat_action(V, lam, Z.T)
-    assert rel(back, R.T) <= 1e-10
+    assert rel(back, R.T) <= 1e-12
 
 
 @pytest.mark.parametrize("method,l", [("randsvd", 20), ("nystrom", 20), ("singleview", 20),
@@ -80,7 +83,7 @@ def test_fp32_sketch_close_to_oracle(small, method, l):
     else:
         lr = sketch.singleview(ref.A, ref.At, Om, Ps)
     X = np.random.default_rng(1).standard_normal((wl.n, 4))
-    assert rel(hhat_action(V, lam, X), hhat_action(lr.V, lr.lam, X)) <= 1e-4
+    assert rel(hhat_action(V, lam, X), hhat_action(lr.V, lr.lam, X)) <= 1e-5
     assert np.max(np.abs(V.T @ V - np.eye(V.shape[1]))) <= 1e-5
 
 
@@ -266,6 +269,57 @@ def test_adaptive_singleview_matches_oracle(small, prec):
     c = prob.counters()
     V, lam = pc.arrays()
     X = np.random.default_rng(11).standard_normal((wl.n, 4))
-    tol = 1e-8 if prec == "fp64" else 1e-4
+    tol = 1e-10 if prec == "fp64" else 1e-5
     assert rel(hhat_action(V, lam, X), hhat_action(lr.V, lr.lam, X)) <= tol
     assert (c["tlm_offline"], c["adj_offline"]) == (lr.tlm, lr.adj) == (24, 49)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adaptive_nystrom_matches_oracle(small, prec):
+    """Adaptive Nystrom (Alg. 2 steps 3-7 redone on the grown sketch; the paper
+    defers this variant to Frangella et al., Sec. 3.1.2) against the oracle,
+    growing 8 -> 24 columns (l_hat = 4): the action of H_hat, the kappa_sk
+    history's final size and the PDE-solve counts. The FP32 sketch shifts with
+    u = 2^-24 and is compared with the oracle run at that u."""
+    import paper_2401_15758_gb300 as g
+    from oracle import philox, sketch, solvers
+    wl, prob, ref = small
+    eps = 2.0 ** -53 if prec == "fp64" else 2.0 ** -24
+    n = wl.n
+    draw_omega = lambda c0, c: philox.gaussian(wl.seed, solvers.STREAM_SKETCH, n, c, col0=c0)
+    draw_v = lambda t: sketch.unit_test_vector(wl.seed, solvers.STREAM_KAPPA, n, index=1 + t)
+    lr = sketch.adaptive_nystrom(ref.misfit_hvp, ref.hvp, draw_omega, 8, 4, 0.5, 24, draw_v, eps=eps)
+    prob.counters_reset()
+    pc = prob.build_precond("nystrom", l=8, adaptive=True, l_hat=4, eps_sk=0.5, l_max=24,
+                            seed=wl.seed, prec=g.FP64 if prec == "fp64" else g.FP32)
+    c = prob.counters()
+    V, lam = pc.arrays()
+    X = np.random.default_rng(12).standard_normal((n, 4))
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert rel(hhat_action(V, lam, X), hhat_action(lr.V, lr.lam, X)) <= tol
+    assert lr.kappa_hist[-1][0] == 24
+    assert (c["tlm_offline"], c["adj_offline"]) == (lr.tlm, lr.adj) == (24, 24)
+
+
+def test_shifted_cholqr_retry_on_a_rank_deficient_sketch(small):
+    """A RandSVD sketch of l = 64 columns of an operator of numerical rank 43
+    (the prior's square root keeps 43 modes): the Gram matrix Y^T Y of the
+    CholeskyQR2 is singular, its Cholesky factorization fails and is redone
+    with a diagonal shift (shifted CholeskyQR3). The result still matches the
+    oracle's Householder-QR RandSVD on the action of H_hat and on the leading
+    eigenvalues, and keeps at most 43 of them."""
+    from oracle import philox, sketch
+    wl, prob, ref = small
+    l = 64
+    Om = philox.gaussian(wl.seed, 100, wl.n, l)
+    prob.counters_reset()
+    pc = prob.build_precond("randsvd", l=l, Omega=torch.tensor(Om.T.copy(), device="cuda"))
+    assert prob.counters()["qr_shifted"] >= 1
+    V, lam = pc.arrays()
+    lr = sketch.randsvd(ref.A, ref.At, Om)
+    X = np.random.default_rng(13).standard_normal((wl.n, 4))
+    assert rel(hhat_action(V, lam, X), hhat_action(lr.V, lr.lam, X)) <= 1e-10
+    lam_ref = np.sort(lr.lam)[::-1]
+    big = lam_ref > 1e-6 * lam_ref[0]
+    assert len(lam) <= 43
+    assert np.max(np.abs(lam[:big.sum()] - lam_ref[big])) <= 1e-10 * lam_ref[0]
