@@ -44,12 +44,12 @@ FP64_PEAK_FMA = 1.20e12   # FP64 FMA throughput measured by a microbenchmark on 
 # recomputation not counted): TLM 52, ADJ 55.
 FLOPS_TLM = 52
 FLOPS_ADJ = 55
-KERNELS = {"tlm": "tlm_f32x2_kernel<8,false>", "adj": "adj_f32x2_kernel<8,false>"}
+KERNELS = {"tlm": "tlm1_kernel<8>", "adj": "adj1_kernel<16>"}
 # DRAM bytes (read + write) per launch of the k=128 FP32 sweeps, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 1280-step profile case
 # (bench.py --profile), scaled by the step count to the 12 800-step launch.
 # Set to None when the kernels change.
-TRAFFIC_PER_LAUNCH = {"tlm": (46.179328e6 + 0.123904e6) * 10, "adj": (44.090624e6 + 0.302080e6) * 10}
+TRAFFIC_PER_LAUNCH = {"tlm": None, "adj": None}
 
 
 def parse():
@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-gn-step", action="store_true", help="skip the time-to-solution part")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bve", action="store_true", help="skip the 256^2 vorticity block of the default run")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "bve_n256", "bve_n1024", "burgers_batch64", "burgers_paper",
                                                              "bve_gyre"],
                     help="the Burgers block (default) or the barotropic vorticity block")
@@ -148,6 +149,61 @@ def oracle_sample(k_sample=8, n_out=40):
     return dt, k_sample / (dt * scale), desc
 
 
+def _oracle_worker(job):
+    """One host process of the parallel oracle sample: FWD over the sample window
+    (untimed), then the timed block (I + H) X of its columns."""
+    n_out, cols = job
+    import sc4dvar_inputs as si
+    from oracle import workload
+    wl = si.burgers_workload(WORKLOAD, n_out=n_out)
+    ref = workload.burgers_problem(wl, si.burgers_draws(wl))
+    ref.set_iterate(np.zeros(wl.n))
+    X = si.gaussian_matrix(wl.seed, wl.n, max(cols) + 1, stream=31)[:, cols]
+    t0 = time.perf_counter()
+    ref.hvp(X)
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_sample_parallel(cols_per_core=2, n_out=40):
+    """The oracle block Hessian product on every host core at once (one process
+    per core, spawned, numpy FP64 single-threaded in each), cols_per_core
+    directions per process over the first n_out output steps. Returns (seconds of
+    the slowest process, HVP/s of all processes scaled to the full window, cores,
+    description)."""
+    import multiprocessing as mp
+    import sc4dvar_inputs as si
+    cores = host_cores()
+    jobs = [(n_out, list(range(c * cols_per_core, (c + 1) * cols_per_core))) for c in range(cores)]
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            secs = pool.map(_oracle_worker, jobs)
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    wl_full = si.burgers_workload(WORKLOAD)
+    wl = si.burgers_workload(WORKLOAD, n_out=n_out)
+    scale = wl_full.n_steps / wl.n_steps
+    dt = max(secs)
+    k = cores * cols_per_core
+    desc = (f"oracle (numpy FP64) (I+H)X on n={wl.n}, {cores} processes x {cols_per_core} directions "
+            f"(k={k}) in parallel, first {wl.n_steps} of {wl_full.n_steps} RK4 steps; HVP/s = k / slowest "
+            f"process, scaled by {scale:g} to the full window")
+    return dt, k / (dt * scale), cores, desc
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -155,9 +211,9 @@ def reference_arm(args):
     import sc4dvar_inputs as si
     wl = si.burgers_workload(WORKLOAD)
     times, vals = [], []
-    desc = ""
+    desc, cores = "", 1
     for i in range(args.warmup + args.steps):
-        dt, v, desc = oracle_sample(k_sample=4, n_out=20)
+        dt, v, cores, desc = oracle_sample_parallel(cols_per_core=1, n_out=20)
         if i >= args.warmup:
             times.append(dt)
             vals.append(v)
@@ -168,7 +224,7 @@ def reference_arm(args):
         "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(wl),
-        "cpu_baseline": {"value": value, "unit": "HVP/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "HVP/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "HVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -227,12 +283,16 @@ def setup_problem(torch, dev):
 BVE_PASSES_PER_STEP = 104
 
 
-def bve_arm(args):
+def bve_block(name, steps, warmup, with_gn=True):
+    """Block Hessian product of a vorticity workload (FP32 sweeps, k = the
+    workload's block) timed with CUDA events (256 MiB L2 flush before every
+    step), the autograd gradient, and optionally the GN step to 1e-6 against
+    plain FP64 CG. Returns a dict."""
     import torch
     import paper_2401_15758_gb300 as g
     import sc4dvar_inputs as si
     dev = torch.device("cuda", 0)
-    wl = si.bve_workload(args.workload)
+    wl = si.bve_workload(name)
     d = si.bve_draws(wl)
     prob = g.Problem.from_bve_workload(wl, d)
     xt = torch.tensor(d["x_true0"], device=dev)
@@ -245,16 +305,13 @@ def bve_arm(args):
     Y = torch.empty_like(X)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.zero_()
         prob.gn_hessian_apply_block(X, prec=g.FP32, out=Y)
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
-    time.sleep(0.3)
     l0 = g.lib.sc4dvar_launch_count()
     ms = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -276,11 +333,10 @@ def bve_arm(args):
         torch.cuda.synchronize()
         if i:
             grad_ms.append(a.elapsed_time(b))
-    clk = clocks.stop()
     t = statistics.mean(ms) / 1e3
     nbytes = BVE_PASSES_PER_STEP * wl.n * 4 * wl.n_steps * k
     gn = None
-    if not args.no_gn_step:
+    if with_gn:
         if wl.n_checkpoints:
             # 1024^2 set-up: Nystrom sketch of the block size (k = 512)
             sk = {"method": "nystrom", "l": k}
@@ -289,23 +345,39 @@ def bve_arm(args):
             sk = {"method": "randsvd", "l": k, "adaptive": True, "l_hat": k // 2, "eps_sk": 1.01}
         gn = gn_step(torch, g, prob, wl, dev, sketch=sk)
     peak = measured_hbm_gbs()
-    out = {"metric": METRIC, "value": k / t, "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"{wl.name}: doubly periodic barotropic vorticity {wl.N}x{wl.N}, "
-                                  f"{wl.n_steps} RK4 steps, m={wl.m}, block k={k}, FP32 sweeps"
-                                  + (f", {wl.n_checkpoints} FP64 checkpoints" if wl.n_checkpoints else ""),
-                      "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": k,
-                      "checkpoints": wl.n_checkpoints,
-                      "l2": "256 MiB write before every timed step"},
+    out = {"value": k / t, "unit": "HVP/s", "ms_per_step": 1e3 * t, "steps": steps, "warmup": warmup,
+           "workload": f"{wl.name}: doubly periodic barotropic vorticity {wl.N}x{wl.N}, "
+                       f"{wl.n_steps} RK4 steps, m={wl.m}, block k={k}, FP32 sweeps"
+                       + (f", {wl.n_checkpoints} FP64 checkpoints" if wl.n_checkpoints else ""),
+           "n": wl.n, "rk_steps": wl.n_steps, "m": wl.m, "k": k, "checkpoints": wl.n_checkpoints,
            "gradient_ms": statistics.mean(grad_ms),
            "roofline": {"bound": "hbm", "kernel": "block Hessian product (all sweep kernels)",
                         "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": nbytes / t / 1e9 / peak, "traffic": None,
-                        "algorithmic_bytes": nbytes},
-           "gpu_launches": int(launches), "clocks": clk}
+                        "algorithmic_bytes": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+           "gpu_launches": int(launches)}
     if gn is not None:
         out["gn_step"] = gn
+    prob.close()
+    return out
+
+
+def bve_arm(args):
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    r = bve_block(args.workload, args.steps, args.warmup, with_gn=not args.no_gn_step)
+    clk = clocks.stop()
+    out = {"metric": METRIC, "value": r["value"], "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": r["workload"], "n": r["n"], "rk_steps": r["rk_steps"], "m": r["m"],
+                      "k": r["k"], "checkpoints": r["checkpoints"],
+                      "l2": "256 MiB write before every timed step"},
+           "gradient_ms": r["gradient_ms"], "roofline": r["roofline"], "gpu_launches": r["gpu_launches"],
+           "clocks": clk}
+    if "gn_step" in r:
+        out["gn_step"] = r["gn_step"]
     print(json.dumps(out), flush=True)
 
 
@@ -693,9 +765,45 @@ def gpu_arm(args):
     e2e = {"value": e2e_val, "unit": "HVP/s", "h2d_bytes_per_step": Xh.numel() * 4,
            "d2h_bytes_per_step": Yh.numel() * 4}
 
+    # the same block through the FP64 and the double-float (DF64) sweeps, and the
+    # error of every FP32 column against the FP64 product (the FP64 path matches
+    # the oracle to 1e-10 in the parity tests)
+    X64 = X.double()
+    prec_var = {}
+    Y64 = None
+    for name, pr in (("fp64", g.FP64), ("df64", g.DF64)):
+        Yv = torch.empty_like(X64)
+        prob.gn_hessian_apply_block(X64, prec=pr, out=Yv)
+        reps = []
+        for _ in range(2):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            prob.gn_hessian_apply_block(X64, prec=pr, out=Yv)
+            b.record(stream)
+            torch.cuda.synchronize()
+            reps.append(a.elapsed_time(b))
+        t_v = statistics.mean(reps) / 1e3
+        prec_var[name] = {"value": k / t_v, "unit": "HVP/s", "ms_per_step": 1e3 * t_v, "steps": 2, "warmup": 1}
+        if name == "fp64":
+            Y64 = Yv
+        else:
+            prec_var[name]["max_column_rel_err_vs_fp64"] = float(
+                (torch.linalg.norm(Yv - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)).max())
+    prec_var["fp32"] = {"value": value, "unit": "HVP/s", "max_column_rel_err_vs_fp64": float(
+        (torch.linalg.norm(Y.double() - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)).max())}
+    del Y64
+
     gn = None
     if not args.no_gn_step:
         gn = gn_step(torch, g, prob, wl, dev)
+
+    # the 256^2 barotropic vorticity block (HBM-bound streaming sweeps) and its
+    # GN step with the adaptive sketch, as an extra measurement on the same GPU
+    bve = None
+    if not args.no_bve and world == 1:
+        prob.close()
+        bve = bve_block("bve_n256", steps=3, warmup=3, with_gn=not args.no_gn_step)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "HVP/s", "n_gpus": world,
@@ -703,12 +811,18 @@ def gpu_arm(args):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic", "config": config_dict(wl), "roofline": roofline,
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+        out["precision_variants"] = prec_var
         if gn is not None:
             out["gn_step"] = gn
+        if bve is not None:
+            out["bve_n256"] = bve
         if not args.no_cpu_baseline:
-            dt, v, desc = oracle_sample()
-            out["cpu_baseline"] = {"value": v, "unit": "HVP/s", "cores": 1, "kind": "oracle",
-                                   "sample": desc, "seconds": dt}
+            dt, v, cores, desc = oracle_sample_parallel()
+            dt1, v1, desc1 = oracle_sample()
+            out["cpu_baseline"] = {"value": v, "unit": "HVP/s", "cores": cores, "kind": "oracle",
+                                   "sample": desc, "seconds": dt,
+                                   "one_thread": {"value": v1, "unit": "HVP/s", "cores": 1,
+                                                  "sample": desc1, "seconds": dt1}}
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

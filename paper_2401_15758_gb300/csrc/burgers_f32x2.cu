@@ -515,8 +515,9 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) tlm1_kernel(
   f2* sm = reinterpret_cast<f2*>(smraw);
   const int H = g.H, NT = blockDim.x, tid = threadIdx.x;
   f2* stage = sm + 2 * H;  // rows t (even / odd) at sm and sm + H
+  f2* carry = stage + H;   // low-order part of the state (my chunks)
   Xch X;
-  X.first = stage + H;
+  X.first = carry + H;
   X.last = X.first + 4 * NT;
   X.NT = NT;
   X.tid = tid;
@@ -542,6 +543,12 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) tlm1_kernel(
     dR = X.swr ? swp(b) : b;
   }
   float* wcol = W + (size_t)col * ldw;
+  {
+    f2 z[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) z[p] = mk(0.f);
+    R::store(carry, tid, NT, z);
+  }
   if (g.N > 0) {
     R::prefetch(sm, trajp + i0, tid, NT);
     R::wait();
@@ -577,7 +584,8 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) tlm1_kernel(
     for (int s = 0; s < 4; ++s) {
       const f2 bs = mk(kB[s]);
       const f2 mha = mk(s < 3 ? -g.h * kA[s] : 0.f);
-      f2 Un[P], Dn[P];
+      f2 Un[P], Dn[P], cy[P];
+      if (s == 3) R::load(carry, tid, NT, cy);
       // pair p from P at p-1, p, p+1 and the forward differences at p (q = p) and p + 1
       auto pair = [&](int p, f2 Pm, f2 Pc, f2 Pn, f2 du0, f2 du1, f2 dd0, f2 dd1) {
         const f2 nM = fma2(c1, U[p], nc2);
@@ -589,7 +597,13 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) tlm1_kernel(
           Un[p] = fma2(mha, gu, x[p]);
           Dn[p] = fma2(mha, G, dx[p]);
         } else {
-          dx[p] = fma2(mh, acc[p], dx[p]);
+          // dx += -h acc with the rounding error of the sum carried to the next
+          // step (Fast2Sum, |dx| >= |increment|): the FP32 state then drifts by
+          // far less than u per step over windows of 10^4 steps
+          const f2 inc = fma2(mh, acc[p], cy[p]);
+          const f2 sum = add2(dx[p], inc);
+          cy[p] = add2(fma2(sum, m1, dx[p]), inc);
+          dx[p] = sum;
         }
       };
       // interior pairs 1 .. P-2, streaming a window of P and differences
@@ -615,6 +629,7 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) tlm1_kernel(
         X.put(par, 1, Dn[0], Dn[P - 1]);
       } else {
         X.put(par, 1, dx[0], dx[P - 1]);
+        R::store(carry, tid, NT, cy);
         R::wait();
       }
       __syncthreads();
@@ -643,10 +658,12 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) adj1_kernel(
   f2* sm = reinterpret_cast<f2*>(smraw);
   const int H = g.H, NT = blockDim.x, tid = threadIdx.x;
   // rows x_r (even / odd r) at sm and sm + H; stage states 1, 2 of the step at
-  // ubuf[0], ubuf[1] (ubuf[0] also stages lambda for the observation forcing)
+  // ubuf[0], ubuf[1] (ubuf[0] also stages lambda for the observation forcing);
+  // the low-order part of lambda's sums (my chunks)
   f2* ubuf[2] = {sm + 2 * H, sm + 3 * H};
+  f2* lam_c = sm + 4 * H;
   Xch X;
-  X.first = sm + 4 * H;
+  X.first = sm + 5 * H;
   X.last = X.first + 4 * NT;
   X.NT = NT;
   X.tid = tid;
@@ -660,11 +677,12 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) adj1_kernel(
   const f2* trajp = reinterpret_cast<const f2*>(traj);
   const float* win = Win + (size_t)col * ldw;
   const f2 c1 = mk(g.c1), c2 = mk(g.c2), nc2 = mk(-g.c2), m1 = mk(-1.f);
-  const f2 h3 = mk(g.h / 3.f), half = mk(0.5f);
+  const f2 h3 = mk(g.h / 3.f), h6 = mk(g.h / 6.f);
   constexpr float kA[3] = {0.5f, 0.5f, 1.0f};
   f2 lam[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) lam[p] = mk(0.f);
+  R::store(lam_c, tid, NT, lam);
   if (g.N > 0) {
     R::prefetch(sm + ((g.N - 1) & 1) * H, trajp + (size_t)(g.N - 1) * H + i0, tid, NT);
     R::wait();
@@ -718,8 +736,7 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) adj1_kernel(
       pair(0, fma2(uL, m1, U[0]), du1);
       const int par = s & 1;
       X.put(par, 0, Un[0], Un[P - 1]);
-      if (s == 2)  // kappa_3 = h/6 lambda' of my edge pairs
-        X.put(par, 1, mul2(half, mul2(h3, lam[0])), mul2(half, mul2(h3, lam[P - 1])));
+      if (s == 2) X.put(par, 1, mul2(h6, lam[0]), mul2(h6, lam[P - 1]));  // kappa_3 = h/6 lambda'
       if (s < 2) R::store(ubuf[s], tid, NT, Un);
       __syncthreads();
       if (s == 0 && r >= 1) R::prefetch(sm + ((r - 1) & 1) * H, trajp + (size_t)(r - 1) * H + i0, tid, NT);
@@ -730,12 +747,10 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) adj1_kernel(
     }
     // backward: kappa_3 = h b_3 lambda', theta_s = F_s^T kappa_s, lambda += theta_s,
     // kappa_{s-1} = h b_{s-1} lambda' + h a_{s-1} theta_s
-    f2 L3[P], K[P];
+    // (h b lambda' is formed where it is used: no register array for it)
+    f2 K[P], th[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-      L3[p] = mul2(h3, lam[p]);
-      K[p] = mul2(half, L3[p]);
-    }
+    for (int p = 0; p < P; ++p) K[p] = mul2(h6, lam[p]);
 #pragma unroll
     for (int s = 3; s >= 0; --s) {
       if (s == 1 || s == 2) rh.get(ubuf[s - 1], uL, uR);
@@ -744,10 +759,10 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) adj1_kernel(
       f2 Kn[P];
       // theta_p = P_{p+1} dk_{p+1} + nM_{p-1} dk_p with dk_q = K_q - K_{q-1}
       auto pair = [&](int p, f2 nMm, f2 Pn, f2 dk0, f2 dk1) {
-        const f2 th = fma2(Pn, dk1, mul2(nMm, dk0));
-        lam[p] = add2(lam[p], th);
-        if (s == 3 || s == 2) Kn[p] = fma2(hA, th, L3[p]);
-        else if (s == 1) Kn[p] = fma2(hA, th, mul2(half, L3[p]));
+        const f2 ts = fma2(Pn, dk1, mul2(nMm, dk0));
+        th[p] = (s == 3) ? ts : add2(th[p], ts);
+        if (s == 3 || s == 2) Kn[p] = fma2(hA, ts, mul2(h3, lam[p]));
+        else if (s == 1) Kn[p] = fma2(hA, ts, mul2(h6, lam[p]));
       };
       const f2 nM0 = fma2(c1, U[0], nc2), dk1 = fma2(K[0], m1, K[1]);
       f2 nMm = nM0, dkm = dk1;
@@ -776,12 +791,29 @@ __global__ void __launch_bounds__(Bounds1<P>::kThreads, 1) adj1_kernel(
         for (int p = 0; p < P; ++p) K[p] = Kn[p];
       }
     }
+    // lambda += sum_s theta_s, the rounding error carried to the next step
+    // (Fast2Sum, as for the tangent-linear state)
+    {
+      f2 cv[P];
+      R::load(lam_c, tid, NT, cv);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const f2 inc = add2(th[p], cv[p]);
+        const f2 sum = add2(lam[p], inc);
+        cv[p] = add2(fma2(sum, m1, lam[p]), inc);
+        lam[p] = sum;
+      }
+      R::store(lam_c, tid, NT, cv);
+    }
   }
+  f2 cv[P];
+  R::load(lam_c, tid, NT, cv);
   float* out = Out + (size_t)col * ldo;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    out[i0 + p] = lam[p].x;
-    out[H + i0 + p] = lam[p].y;
+    const f2 l = add2(lam[p], cv[p]);
+    out[i0 + p] = l.x;
+    out[H + i0 + p] = l.y;
   }
 }
 
@@ -797,7 +829,8 @@ int pairs_per_thread(int Hs, int tuned, bool adj = false) {
     return e ? atoi(e) : 0;
   }();
   const int dflt = (adj && Hs == 4096) ? 16 : std::max(1, std::min(8, Hs / 512));
-  int P = tuned > 0 ? tuned : (forced > 0 ? forced : dflt);
+  // the tuned shape is the tangent-linear sweep's; the adjoint keeps 16 at 4096 pairs
+  int P = (tuned > 0 && !(adj && Hs == 4096)) ? tuned : (forced > 0 ? forced : dflt);
   if (P == 16 && Hs % 16 == 0 && Hs / 16 >= 64 && Hs / 16 <= 256) return P;  // one-CTA sweeps only
   if (P != 1 && P != 2 && P != 4 && P != 8) P = 8;
   while (P > 1 && Hs / P < 32) P /= 2;
@@ -883,8 +916,8 @@ int burgers_tlm_f32x2(const ModelGeom& m, const float* traj_folded, const float*
   int P = pairs_per_thread(g.Hs, m.pairs_tuned);
   if (cl > 1 && P > 8) P = 8;
   int NT = g.Hs / P;
-  if (cl == 1 && P >= 4 && NT <= 512) {
-    const size_t sm1 = (size_t)(3 * H + 8 * NT) * sizeof(f2);
+  const size_t sm1 = (size_t)(4 * H + 8 * NT) * sizeof(f2);
+  if (cl == 1 && P >= 4 && NT <= 512 && sm1 <= kMaxSmem2) {
     if (P == 4) SC4_TRY(launch2(tlm1_kernel<4>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw));
     else if (P == 16) SC4_TRY(launch2(tlm1_kernel<16>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw));
     else SC4_TRY(launch2(tlm1_kernel<8>, k, NT, sm1, 1, st, g, traj_folded, U0, ldu, W, ldw));
@@ -910,8 +943,8 @@ int burgers_adj_f32x2(const ModelGeom& m, const float* traj_folded, const float*
   int P = pairs_per_thread(g.Hs, m.pairs_tuned, true);
   if (cl > 1 && P > 8) P = 8;
   int NT = g.Hs / P;
-  if (cl == 1 && P >= 4 && NT <= 512) {
-    const size_t sm1 = (size_t)(4 * H + 8 * NT) * sizeof(f2);
+  const size_t sm1 = (size_t)(5 * H + 8 * NT) * sizeof(f2);
+  if (cl == 1 && P >= 4 && NT <= 512 && sm1 <= kMaxSmem2) {
     if (P == 4) SC4_TRY(launch2(adj1_kernel<4>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo));
     else if (P == 16) SC4_TRY(launch2(adj1_kernel<16>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo));
     else SC4_TRY(launch2(adj1_kernel<8>, k, NT, sm1, 1, st, g, traj_folded, Win, ldw, Out, ldo));
