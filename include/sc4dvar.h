@@ -46,9 +46,8 @@ extern "C" {
 #define SC4DVAR_ERR_NOT_SPD       -3   /* a Cholesky factorization failed        */
 #define SC4DVAR_ERR_BREAKDOWN     -4   /* PCG: p^T (I+H) p <= 0 or not finite     */
 #define SC4DVAR_ERR_NOT_CONVERGED -5   /* PCG: maxit reached above tolerance      */
-#define SC4DVAR_ERR_TIMEOUT       -6   /* reserved for a bounded device wait that
-                                           gives up; no kernel of this version waits
-                                           on another, so no call returns it        */
+#define SC4DVAR_ERR_TIMEOUT       -6   /* a bounded device wait gave up (the tensor-
+                                           core tall products wait on their MMAs)    */
 #define SC4DVAR_ERR_OOM           -7
 #define SC4DVAR_ERR_STATE         -8   /* e.g. no forward trajectory stored yet   */
 
@@ -163,7 +162,18 @@ typedef struct {
     uint64_t seed;         /* Philox key                                          */
     int gn_iter;           /* GN iteration index k (selects the Philox streams)   */
     int prec;              /* SC4DVAR_FP64 / SC4DVAR_FP32 sweeps and sketch storage */
+    int gemm;              /* FP32 sketches: arithmetic of the tall products with an
+                              l x l factor (Q = Y R^{-1}, V = W^T U S^{-1}, W = L^{-1} Y^T,
+                              Gram-Schmidt updates): SC4DVAR_GEMM_*. Gram matrices
+                              stay FP64-accurate in every mode.                        */
 } sc4dvar_sketch_opts;
+
+/* Tall-product arithmetic of FP32 sketches (sc4dvar_sketch_opts.gemm). */
+#define SC4DVAR_GEMM_3XTF32 0   /* tensor cores, three TF32 products per term (hi*hi +
+                                   hi*lo + lo*hi): FP32 accuracy (default)          */
+#define SC4DVAR_GEMM_SIMT   1   /* CUDA cores, FP32 fused multiply-adds             */
+#define SC4DVAR_GEMM_TF32   2   /* tensor cores, one TF32 product (~1e-4 relative)   */
+#define SC4DVAR_GEMM_BF16   3   /* tensor cores, BF16 inputs (~1e-3 relative)        */
 
 typedef struct {
     double tol;            /* relative residual |r|/|b| of the recurrence residual  */
@@ -310,6 +320,19 @@ int sc4dvar_gn_hessian_apply_block_noalloc(sc4dvar_problem_t p, const void* X_de
  * adaptive forms). Omega_dev (n x l, double, ld n) may be NULL (then drawn with
  * Philox from opts->seed / gn_iter); Psi_dev likewise (m x l2). Synchronizes.
  * ERR_NOT_SPD if a Cholesky factorization fails. */
+/* The sketches' tall product on its own: C (rows x c) = alpha A op(B) + beta C
+ * with A (rows x kk, FP32, column-major, ld lda), B FP64 (kk x c, ld ldb; or
+ * c x kk when transB != 0) and C FP32 (c_double = 0) or FP64 (c_double = 1),
+ * column-major with ld ldc; mode SC4DVAR_GEMM_*. All pointers are device
+ * memory owned by the caller. The products of Algs. 1-5 with an l x l factor
+ * (CholeskyQR's Q = Y R^{-1}, the thin SVD's V = W^T U S^{-1}, ...) run through
+ * it; in the tensor-core modes one CTA computes 128 rows x 256 columns with
+ * tcgen05 MMAs accumulating in tensor memory. Synchronizes; SC4DVAR_ERR_TIMEOUT
+ * if a bounded wait on the tensor cores gave up. */
+int sc4dvar_tall_gemm(int mode, int rows, int kk, int c, double alpha, const float* A_dev, int lda,
+                      const double* B_dev, int ldb, int transB, double beta, void* C_dev, int c_double,
+                      int ldc, void* stream);
+
 int sc4dvar_build_precond(sc4dvar_problem_t p, const sc4dvar_sketch_opts* opts,
                           const double* Omega_dev, const double* Psi_dev,
                           sc4dvar_precond_t* out, void* stream);

@@ -12,9 +12,9 @@ import ctypes as C
 import numpy as np
 
 from . import _abi
-from ._abi import (DF64, FP32, FP64, MODEL_BURGERS1D, PRIOR_SE, PRIOR_SYMBOL, SKETCH_NONE,  # noqa: F401
-                   SKETCH_NYSTROM, SKETCH_RANDSVD, SKETCH_SINGLEVIEW, STREAM_KAPPA, STREAM_PSI,
-                   STREAM_SKETCH, Sc4dvarError)
+from ._abi import (DF64, FP32, FP64, GEMM_3XTF32, GEMM_BF16, GEMM_SIMT, GEMM_TF32,  # noqa: F401
+                   MODEL_BURGERS1D, PRIOR_SE, PRIOR_SYMBOL, SKETCH_NONE, SKETCH_NYSTROM, SKETCH_RANDSVD,
+                   SKETCH_SINGLEVIEW, STREAM_KAPPA, STREAM_PSI, STREAM_SKETCH, Sc4dvarError)
 
 lib = _abi.load()
 check = _abi.check
@@ -262,10 +262,11 @@ class Problem:
 
     def build_precond(self, method="randsvd", l=20, l2=0, adaptive=False, l_hat=0, l_max=0,
                       eps_sk=1.01, seed=20240128, gn_iter=0, prec=FP64, Omega=None, Psi=None,
-                      stream=None):
-        """Sketch H at the stored iterate (Algs. 1-5). Omega: (l, n) float64 rows = columns."""
+                      stream=None, gemm=0):
+        """Sketch H at the stored iterate (Algs. 1-5). Omega: (l, n) float64 rows = columns.
+        gemm: tall-product arithmetic of FP32 sketches (GEMM_3XTF32, GEMM_SIMT, ...)."""
         o = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed,
-                            gn_iter, prec)
+                            gn_iter, prec, gemm)
         h = C.c_void_p()
         Om = None if Omega is None else Omega.contiguous()
         Ps = None if Psi is None else Psi.contiguous()
@@ -292,9 +293,10 @@ class Problem:
     def gauss_newton(self, v, iters=3, method="none", l=20, adaptive=False, l2=0, l_hat=0,
                      l_max=0, eps_sk=1.01, eps_re=10.0, tol=1e-6, maxit=0, prec=FP64, refine=2,
                      gtol=0.0, seed=20240128, line_search=False, ls_c1=1e-4, ls_c2=0.9,
-                     ls_alpha1=1.0, solve="pcg", stream=None):
+                     ls_alpha1=1.0, solve="pcg", stream=None, gemm=0):
         """Gauss-Newton in place on v (float64, (n,)); returns the per-iteration record."""
-        so = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed, 0, prec)
+        so = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed, 0, prec,
+                             gemm)
         o = _abi.GnOpts(iters, gtol, so, eps_re, _abi.PcgOpts(tol, maxit, prec, refine), int(line_search),
                         ls_c1, ls_c2, ls_alpha1, {"pcg": 0, "sketchsolv": 1}[solve])
         info = _abi.GnInfo()
@@ -425,6 +427,23 @@ def gaussian(seed, stream_id, rows, cols, col0=0, stream=None):
     out = torch.empty((cols, rows), dtype=torch.float64, device="cuda")
     check(lib.sc4dvar_gaussian(seed, stream_id, rows, cols, col0, _ptr(out), _stream(stream)))
     return out
+
+
+def tall_gemm(A, B, mode=GEMM_3XTF32, transB=False, alpha=1.0, beta=0.0, C=None, out_dtype=None,
+              stream=None):
+    """C = alpha A op(B) + beta C with the sketches' tall product. Column-major
+    shapes as (cols, rows) row-major tensors: A (kk, rows) float32, B (c, kk)
+    float64 (B (kk, c) when transB), C (c, rows) float32 or float64."""
+    torch = _torch()
+    kk, rows = A.shape
+    c = B.shape[1] if transB else B.shape[0]
+    assert (B.shape[0] if transB else B.shape[1]) == kk
+    if C is None:
+        C = torch.zeros((c, rows), dtype=out_dtype or torch.float32, device="cuda")
+    cd = 1 if C.dtype == torch.float64 else 0
+    check(lib.sc4dvar_tall_gemm(mode, rows, kk, c, alpha, _ptr(A), rows, _ptr(B), B.shape[1], int(transB),
+                                beta, _ptr(C), cd, rows, _stream(stream)))
+    return C
 
 
 def qr_update(P, B, Q1, R1, r1, k1, stream=None):

@@ -26,6 +26,7 @@ PRIOR_DIRICHLET_INV_HELMHOLTZ = 3
 FP64 = 0
 FP32 = 1
 DF64 = 2      # double blocks, double-float sweeps (periodic Burgers Hessian products)
+GEMM_3XTF32, GEMM_SIMT, GEMM_TF32, GEMM_BF16 = 0, 1, 2, 3
 PRIOR_SYMBOL = 0
 PRIOR_SE = 1
 PRIOR_INV_HELMHOLTZ = 2
@@ -56,7 +57,7 @@ class SketchOpts(C.Structure):
     _fields_ = [
         ("method", C.c_int), ("l", C.c_int), ("l2", C.c_int), ("adaptive", C.c_int),
         ("l_hat", C.c_int), ("l_max", C.c_int), ("eps_sk", C.c_double),
-        ("seed", C.c_uint64), ("gn_iter", C.c_int), ("prec", C.c_int),
+        ("seed", C.c_uint64), ("gn_iter", C.c_int), ("prec", C.c_int), ("gemm", C.c_int),
     ]
 
 
@@ -118,6 +119,7 @@ SIGNATURES = {
     "sc4dvar_gn_hessian_apply_block": (I, [P, P, I, I, P, I, I, I, P]),
     "sc4dvar_gn_hessian_apply_block_noalloc": (I, [P, P, I, I, P, I, I, I, P]),
     "sc4dvar_build_precond": (I, [P, C.POINTER(SketchOpts), P, P, C.POINTER(P), P]),
+    "sc4dvar_tall_gemm": (I, [I, I, I, I, D, P, I, P, I, I, D, P, I, I, P]),
     "sc4dvar_precond_destroy": (I, [P]),
     "sc4dvar_precond_info": (I, [P, C.POINTER(I), P, P]),
     "sc4dvar_precond_apply": (I, [P, P, I, I, P, I, P]),

@@ -10,6 +10,7 @@
 #include <vector>
 #include "common.cuh"
 #include "dense.cuh"
+#include "tall_tc.cuh"
 #include "dfloat.cuh"
 #include "fft.cuh"
 #include "model.cuh"
@@ -406,11 +407,25 @@ static int host_scalar(Prob* P, double* out, cudaStream_t st) {
 struct SketchWS {
   Buf a, b, c, g, g2, u, w, info, jw;
   int64_t* shifted = nullptr;  // problem counter of shifted CholeskyQR retries
+  int tall = kTall3xTF32;      // arithmetic of the FP32 tall products (sketch_opts.gemm)
   void release() {
     a.release(); b.release(); c.release(); g.release(); g2.release(); u.release(); w.release();
     info.release(); jw.release();
   }
 };
+
+// A tall product with an l x l factor: FP32 sketch matrices with several
+// columns go to the tensor cores in the sketch's mode (or the CUDA-core kernel
+// when asked); FP64 operands and single vectors keep the FP64 / CUDA-core path.
+template <typename T, typename TC>
+static int tall_nn(const SketchWS& ws, int rows, int kk, int c, double alpha, const T* A, int lda,
+                   const double* B, int ldb, int transB, double beta, TC* C, int ldc, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (c > 1 && kk > 0 && ws.tall != kTallSIMT)
+      return tall_gemm_tc<TC>(ws.tall, rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, st);
+  }
+  return gemm_nn<T, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, st);
+}
 
 static int check_info(Buf& info, const char* what, cudaStream_t st) {
   int h = 0;
@@ -425,7 +440,8 @@ static int check_info(Buf& info, const char* what, cudaStream_t st) {
 
 // One CholeskyQR pass: G = src^T src (FP64), L = chol(G), dst = src L^{-T}.
 // When allowed, a failed factorization is retried with the diagonal shift
-// 11 (rows l + l(l+1)) u tr(G) (shifted CholeskyQR; tr(G) >= |G|_2).
+// 11 (rows l + l(l+1)) u tr(G) (shifted CholeskyQR, Fukaya et al. 2020;
+// tr(G) >= |G|_2), u = 2^-53.
 template <typename T>
 static int cholqr_pass(int rows, int l, const T* src, int lds, T* dst, int ldd, bool allow_shift,
                        bool* shifted, SketchWS& ws, cudaStream_t st) {
@@ -444,7 +460,11 @@ static int cholqr_pass(int rows, int l, const T* src, int lds, T* dst, int ldd, 
     SC4_CUDA(cudaStreamSynchronize(st));
     double tr = 0;
     for (int i = 0; i < l; ++i) tr += hg[(size_t)i * l + i];
-    double u = (sizeof(T) == 4) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    // u is the unit roundoff of the Gram matrix, which is FP64-accurate for FP32
+    // data as well (products accumulated exactly in double-float): with the FP32
+    // roundoff the shift would exceed tr(G) at rows l ~ 10^7 and wipe out the
+    // factorization.
+    const double u = std::ldexp(1.0, -53);
     double shift = 11.0 * ((double)rows * l + (double)l * (l + 1)) * u * tr;
     symmetrize_kernel<<<div_up(l * l, 256), 256, 0, st>>>(l, G, l, shift);
     SC4_LAUNCH_CHECK();
@@ -455,7 +475,7 @@ static int cholqr_pass(int rows, int l, const T* src, int lds, T* dst, int ldd, 
   }
   if (s != SC4DVAR_OK) return s;
   SC4_TRY(trtri_lower(l, G, l, Li, l, 0.0, st));
-  return gemm_nn<T, T>(rows, l, l, 1.0, src, lds, Li, l, 1, 0.0, dst, ldd, st);
+  return tall_nn<T, T>(ws, rows, l, l, 1.0, src, lds, Li, l, 1, 0.0, dst, ldd, st);
 }
 
 // Thin QR Y = Q R by CholeskyQR2 (Q separate from Y; a third pass when the
@@ -516,7 +536,7 @@ static int finalize_svd(Prob* P, int l, const T* Wt, int ldw, double nu, double 
   double* B = G;  // reuse: l x r
   svd_scale_kernel<<<div_up(l * r, 256), 256, 0, st>>>(l, r, Us, l, ws_, nu, B, out->lam, out->dsc);
   SC4_LAUNCH_CHECK();
-  SC4_TRY(gemm_nn<T, double>(n, l, r, 1.0, Wt, ldw, B, l, 0, 0.0, out->V, n, st));
+  SC4_TRY(tall_nn<T, double>(ws, n, l, r, 1.0, Wt, ldw, B, l, 0, 0.0, out->V, n, st));
   return SC4DVAR_OK;
 }
 
@@ -631,6 +651,7 @@ static int build_randsvd(Prob* P, const sc4dvar_sketch_opts& o, const double* Om
   const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
   SketchWS ws;
   ws.shifted = &P->counters.qr_shifted;
+  ws.tall = o.gemm;
   Buf Om, Y, Qall, Wt, tmp;
   int rc = SC4DVAR_OK;
   auto body = [&]() -> int {
@@ -660,7 +681,7 @@ static int build_randsvd(Prob* P, const sc4dvar_sketch_opts& o, const double* Om
         SC4_TRY(ws.b.ensure((size_t)l * lh * sizeof(double)));
         for (int pass = 0; pass < 2; ++pass) {
           SC4_TRY(gemm_tn<T, T>(m, l, lh, 1.0, Q, m, yh, m, 0.0, ws.b.as<double>(), l, st));
-          SC4_TRY(gemm_nn<T, T>(m, l, lh, -1.0, Q, m, ws.b.as<double>(), l, 0, 1.0, yh, m, st));
+          SC4_TRY(tall_nn<T, T>(ws, m, l, lh, -1.0, Q, m, ws.b.as<double>(), l, 0, 1.0, yh, m, st));
         }
         SC4_TRY(cholqr2<T>(m, lh, yh, m, Q + (size_t)m * l, m, ws, st));
         SC4_TRY(adj_block<T>(P, Q + (size_t)m * l, m, lh, wt + (size_t)n * l, n, (const T*)nullptr, 0, st));
@@ -704,7 +725,7 @@ static int nystrom_core(Prob* P, int l, const T* om, T* y, double eps, Prec* out
   SC4_TRY(trtri_lower(l, G, l, Li, l, 0.0, st));
   SC4_TRY(ws.a.ensure((size_t)n * l * sizeof(T)));
   T* wt = ws.a.as<T>();
-  SC4_TRY(gemm_nn<T, T>(n, l, l, 1.0, y, n, Li, l, 1, 0.0, wt, n, st));
+  SC4_TRY(tall_nn<T, T>(ws, n, l, l, 1.0, y, n, Li, l, 1, 0.0, wt, n, st));
   double drop = (sizeof(T) == 4) ? 1e-12 : 1e-15;
   return finalize_svd<T>(P, l, wt, n, nu, drop, out, ws, st);
 }
@@ -722,6 +743,7 @@ static int build_nystrom(Prob* P, const sc4dvar_sketch_opts& o, const double* Om
   const double eps = (sizeof(T) == 4) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
   SketchWS ws;
   ws.shifted = &P->counters.qr_shifted;
+  ws.tall = o.gemm;
   Buf Om, Y, Yc, tmp;
   auto body = [&]() -> int {
     SC4_TRY(Om.ensure((size_t)n * lmax * sizeof(T)));
@@ -851,7 +873,7 @@ static int singleview_W(Prob* P, int l1, int l2, const double* Qm, int ldq, cons
   SC4_TRY(trtri_lower(l1, Lt, l1, Li, l1, 0.0, st));                                 // R_M^{-T}
   SC4_TRY(gemm_nn<double, double>(l2, l1, l1, 1.0, Qm, ldq, Li, l1, 0, 0.0, Bm, l2, st));
   // W^T = Z Bm  (n x l1)
-  SC4_TRY(gemm_nn<T, T>(n, l2, l1, 1.0, Z, n, Bm, l2, 0, 0.0, wt, n, st));
+  SC4_TRY(tall_nn<T, T>(ws, n, l2, l1, 1.0, Z, n, Bm, l2, 0, 0.0, wt, n, st));
   return SC4DVAR_OK;
 }
 
@@ -871,6 +893,7 @@ static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double*
   const uint64_t s_ka = SC4DVAR_STREAM_KAPPA + (uint64_t)o.gn_iter;
   SketchWS ws;
   ws.shifted = &P->counters.qr_shifted;
+  ws.tall = o.gemm;
   Buf Om, Ps, Y, QY, Z, Wt, tmp, Mq, Mr, Mb;
   const int ldq = l2max, ldr = lmax;  // Q_M (l2 x l1) and R_M (l1 x l1) at their largest
   auto body = [&]() -> int {
@@ -912,12 +935,13 @@ static int build_singleview(Prob* P, const sc4dvar_sketch_opts& o, const double*
         SC4_TRY(ws.c.ensure((size_t)l1 * lh1 * sizeof(double)));
         for (int pass = 0; pass < 2; ++pass) {
           SC4_TRY(gemm_tn<T, T>(m, l1, lh1, 1.0, qy, m, yh, m, 0.0, ws.c.as<double>(), l1, st));
-          SC4_TRY(gemm_nn<T, T>(m, l1, lh1, -1.0, qy, m, ws.c.as<double>(), l1, 0, 1.0, yh, m, st));
+          SC4_TRY(tall_nn<T, T>(ws, m, l1, lh1, -1.0, qy, m, ws.c.as<double>(), l1, 0, 1.0, yh, m, st));
         }
         {
           // QR of the new block into Q_Y's next columns (cholqr2 needs its own c buffer)
           SketchWS ws2;
           ws2.shifted = &P->counters.qr_shifted;
+          ws2.tall = o.gemm;
           int s2 = cholqr2<T>(m, lh1, yh, m, qy + (size_t)m * l1, m, ws2, st);
           cudaStreamSynchronize(st);
           ws2.release();
@@ -1112,6 +1136,7 @@ static int build_precond_impl(Prob* P, const sc4dvar_sketch_opts& o, const doubl
   }
   SC4_ARG(o.l >= 1 && o.l <= P->n, "sketch size l must be in [1, n]");
   SC4_ARG(o.prec == SC4DVAR_FP64 || o.prec == SC4DVAR_FP32, "prec");
+  SC4_ARG(o.gemm >= SC4DVAR_GEMM_3XTF32 && o.gemm <= SC4DVAR_GEMM_BF16, "gemm mode");
   Prec* pc = new Prec();
   int saved = P->count_mode;
   P->count_mode = kOffline;
@@ -1133,6 +1158,7 @@ static int build_precond_impl(Prob* P, const sc4dvar_sketch_opts& o, const doubl
       rc = SC4DVAR_ERR_INVALID_ARG;
   }
   P->count_mode = saved;
+  if (rc == SC4DVAR_OK && f32) rc = tall_tc_take_error();
   if (rc != SC4DVAR_OK) {
     if (pc->V) cudaFree(pc->V);
     if (pc->lam) cudaFree(pc->lam);
@@ -1586,6 +1612,24 @@ int sc4dvar_build_precond(sc4dvar_problem_t P, const sc4dvar_sketch_opts* o, con
                           const double* Ps, sc4dvar_precond_t* out, void* stream) {
   SC4_ARG(P && o && out, "null argument");
   return build_precond_impl(P, *o, Om, Ps, out, S(stream));
+}
+
+int sc4dvar_tall_gemm(int mode, int rows, int kk, int c, double alpha, const float* A, int lda, const double* B,
+                      int ldb, int transB, double beta, void* C, int c_double, int ldc, void* stream) {
+  SC4_ARG(mode >= SC4DVAR_GEMM_3XTF32 && mode <= SC4DVAR_GEMM_BF16, "gemm mode");
+  SC4_ARG(rows >= 0 && kk >= 0 && c >= 0, "sizes");
+  SC4_ARG(rows == 0 || c == 0 || (A && B && C), "pointers");
+  SC4_ARG(lda >= std::max(rows, 1) && ldc >= std::max(rows, 1) && ldb >= std::max(transB ? c : kk, 1),
+          "leading dimensions");
+  cudaStream_t st = S(stream);
+  SketchWS ws;
+  ws.tall = mode;
+  if (c_double)
+    SC4_TRY(tall_nn<float, double>(ws, rows, kk, c, alpha, A, lda, B, ldb, transB, beta, (double*)C, ldc, st));
+  else
+    SC4_TRY(tall_nn<float, float>(ws, rows, kk, c, alpha, A, lda, B, ldb, transB, beta, (float*)C, ldc, st));
+  SC4_CUDA(cudaStreamSynchronize(st));
+  return tall_tc_take_error();
 }
 
 int sc4dvar_precond_destroy(sc4dvar_precond_t pc) {

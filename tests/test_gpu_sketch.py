@@ -323,3 +323,24 @@ def test_shifted_cholqr_retry_on_a_rank_deficient_sketch(small):
     big = lam_ref > 1e-6 * lam_ref[0]
     assert len(lam) <= 43
     assert np.max(np.abs(lam[:big.sum()] - lam_ref[big])) <= 1e-10 * lam_ref[0]
+
+
+@pytest.mark.parametrize("gemm,tol", [(2, 5e-3), (3, 5e-2), (1, 1e-5)])
+def test_fp32_sketch_with_other_tall_product_arithmetic(small, gemm, tol):
+    """FP32 RandSVD with the tall products in TF32 (gemm = 2) or BF16 (3) on the
+    tensor cores, or on the CUDA cores (1): the action of H_hat against the FP64
+    oracle within the accuracy of that arithmetic, and PCG preconditioned by it
+    still converges in a handful of iterations."""
+    import paper_2401_15758_gb300 as g
+    from oracle import philox, sketch
+    wl, prob, ref = small
+    Om = philox.gaussian(wl.seed, 100, wl.n, 20)
+    pc = prob.build_precond("randsvd", l=20, prec=g.FP32, gemm=gemm,
+                            Omega=torch.tensor(Om.T.copy(), device="cuda"))
+    V, lam = pc.arrays()
+    lr = sketch.randsvd(ref.A, ref.At, Om)
+    X = np.random.default_rng(1).standard_normal((wl.n, 4))
+    assert rel(hhat_action(V, lam, X), hhat_action(lr.V, lr.lam, X)) <= tol
+    b = torch.tensor(np.random.default_rng(2).standard_normal(wl.n), device="cuda")
+    x, info = prob.pcg(b, pc, tol=1e-8)
+    assert info["status"] == 0 and info["iterations"] <= 12
