@@ -40,8 +40,10 @@ K_BLOCK = 128
 FP32_PEAK_ALU = 152 * 128 * 2 * 2.070e9   # FMA lanes x 2 flops x max SM clock (flop/s)
 FP64_PEAK_FMA = 1.20e12   # FP64 FMA throughput measured by a microbenchmark on the same GB300s (flop/s)
 # Algorithmic FP32 flops per grid point per RK4 step of one direction, counted
-# from the tangent-linear / adjoint formulas of the sweeps (base-state stage
-# recomputation not counted): TLM 52, ADJ 55.
+# from the expanded tangent-linear / adjoint stencil formulas (base-state stage
+# recomputation not counted): TLM 52, ADJ 55. The kernels evaluate factored
+# forms of the same operators with fewer operations, so these counts are the
+# method's work, not the instructions executed.
 FLOPS_TLM = 52
 FLOPS_ADJ = 55
 KERNELS = {"tlm": "tlm1_kernel<8>", "adj": "adj1_kernel<16>"}
@@ -49,7 +51,7 @@ KERNELS = {"tlm": "tlm1_kernel<8>", "adj": "adj1_kernel<16>"}
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 1280-step profile case
 # (bench.py --profile), scaled by the step count to the 12 800-step launch.
 # Set to None when the kernels change.
-TRAFFIC_PER_LAUNCH = {"tlm": None, "adj": None}
+TRAFFIC_PER_LAUNCH = {"tlm": (46.178560e6 + 0.083712e6) * 10, "adj": (44.093696e6 + 0.191488e6) * 10}
 
 
 def parse():
@@ -68,6 +70,9 @@ def parse():
                     help="GN iterations of the double-gyre experiment (the paper runs 25)")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
+    ap.add_argument("--profile-sketch", action="store_true",
+                    help="for ncu: two FP32 RandSVD l = 128 sketches of the n = 8192 workload (a warm-up "
+                         "and the profiled one), the sketch of the GN-step comparison")
     return ap.parse_args()
 
 
@@ -896,6 +901,19 @@ def profile_case():
     print("profile case done")
 
 
+def profile_case_sketch():
+    """Two FP32 RandSVD sketches (l = 128) at the background of the n = 8192
+    workload: the sketch phase of the GN step, for a launch list."""
+    import torch
+    dev = torch.device("cuda", 0)
+    g, si, wl, prob, J0 = setup_problem(torch, dev)
+    for _ in range(2):
+        pc = prob.build_precond(method="randsvd", l=K_BLOCK, prec=g.FP32, seed=wl.seed)
+        torch.cuda.synchronize()
+        pc.close()
+    print("sketch profile case done")
+
+
 def profile_case_bve(name="bve_n256"):
     """One FP32 TLM block and one FP32 ADJ block of a vorticity workload on its
     first RK4 steps: 256^2 (k = 256) 20 steps; 1024^2 (k = 512) 16 steps with 4
@@ -939,6 +957,9 @@ def profile_case_gyre():
 
 def main():
     args = parse()
+    if args.profile_sketch:
+        profile_case_sketch()
+        return
     if args.profile:
         if args.workload == "bve_gyre":
             profile_case_gyre()
