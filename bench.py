@@ -67,7 +67,8 @@ def parse():
                                                              "bve_gyre"],
                     help="the Burgers block (default) or the barotropic vorticity block")
     ap.add_argument("--gn-iters", type=int, default=25,
-                    help="GN iterations of the double-gyre experiment (the paper runs 25)")
+                    help="GN iterations of the double-gyre experiment (the paper runs 25) and of the "
+                         "1024^2 vorticity comparison (its workload: 5)")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
     ap.add_argument("--profile-sketch", action="store_true",
@@ -288,7 +289,35 @@ def setup_problem(torch, dev):
 BVE_PASSES_PER_STEP = 104
 
 
-def bve_block(name, steps, warmup, with_gn=True):
+def gn_run_comparison(torch, g, prob, wl, dev, iters, sketch):
+    """Time to solution of `iters` Gauss-Newton iterations from v = 0, each step
+    solved to a 1e-6 relative residual: the sketched method (FP32 sketch reused
+    while kappa_re < eps_re = 10, Eq. condtext2, FP32-operator PCG with FP64
+    defect correction) against plain FP64 CG (Prec_Gamma). FWD and gradients
+    are inside both times."""
+    res = {}
+    for name, opts in (("method", dict(prec=g.FP32, **sketch)), ("plain_fp64_cg", dict(method="none"))):
+        prob.counters_reset()
+        v = torch.zeros(wl.n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rec = prob.gauss_newton(v, iters=iters, tol=1e-6, seed=wl.seed, **opts)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        c = prob.counters()
+        res[name] = {"seconds": secs, "pcg_its": [r["pcg_its"] for r in rec],
+                     "sketched": [bool(r["sketched"]) for r in rec], "rank": [r["rank"] for r in rec],
+                     "kappa_re": [r["kappa_re"] for r in rec], "J": [r["J"] for r in rec],
+                     "relres": [r["relres"] for r in rec], "counters": c}
+        print(f"{name}: {json.dumps(res[name])}", file=sys.stderr, flush=True)
+    res["speedup"] = res["plain_fp64_cg"]["seconds"] / res["method"]["seconds"]
+    res["iters"] = iters
+    res["sketch"] = dict(sketch)
+    res["unit"] = "s"
+    return res
+
+
+def bve_block(name, steps, warmup, with_gn=True, gn_iters=0):
     """Block Hessian product of a vorticity workload (FP32 sweeps, k = the
     workload's block) timed with CUDA events (256 MiB L2 flush before every
     step), the autograd gradient, and optionally the GN step to 1e-6 against
@@ -341,7 +370,7 @@ def bve_block(name, steps, warmup, with_gn=True):
     t = statistics.mean(ms) / 1e3
     nbytes = BVE_PASSES_PER_STEP * wl.n * 4 * wl.n_steps * k
     gn = None
-    if with_gn:
+    if with_gn and gn_iters <= 1:
         if wl.n_checkpoints:
             # 1024^2 set-up: Nystrom sketch of the block size (k = 512)
             sk = {"method": "nystrom", "l": k}
@@ -349,6 +378,13 @@ def bve_block(name, steps, warmup, with_gn=True):
             # SketchPrecA set-up: adaptive RandSVD from l0 = k, growing by k/2 to eps_sk = 1.01
             sk = {"method": "randsvd", "l": k, "adaptive": True, "l_hat": k // 2, "eps_sk": 1.01}
         gn = gn_step(torch, g, prob, wl, dev, sketch=sk)
+    gn_multi = None
+    if with_gn and gn_iters > 1:
+        # the sketch of the block size reused across the GN iterations under the
+        # reuse rule (adaptive with l_max = l: reuse without growth)
+        gn_multi = gn_run_comparison(torch, g, prob, wl, dev, gn_iters,
+                                     {"method": "nystrom", "l": k, "adaptive": True, "l_max": k,
+                                      "eps_re": 10.0})
     peak = measured_hbm_gbs()
     out = {"value": k / t, "unit": "HVP/s", "ms_per_step": 1e3 * t, "steps": steps, "warmup": warmup,
            "workload": f"{wl.name}: doubly periodic barotropic vorticity {wl.N}x{wl.N}, "
@@ -359,10 +395,12 @@ def bve_block(name, steps, warmup, with_gn=True):
            "roofline": {"bound": "hbm", "kernel": "block Hessian product (all sweep kernels)",
                         "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": nbytes / t / 1e9 / peak, "traffic": None,
-                        "algorithmic_bytes": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                        "algorithmic_bytes": nbytes, "peak_source": hbm_peak()[1]},
            "gpu_launches": int(launches)}
     if gn is not None:
         out["gn_step"] = gn
+    if gn_multi is not None:
+        out["gn_iterations"] = gn_multi
     prob.close()
     return out
 
@@ -371,7 +409,8 @@ def bve_arm(args):
     clocks = ClockSampler(0)
     clocks.start()
     time.sleep(0.3)
-    r = bve_block(args.workload, args.steps, args.warmup, with_gn=not args.no_gn_step)
+    r = bve_block(args.workload, args.steps, args.warmup, with_gn=not args.no_gn_step,
+                  gn_iters=args.gn_iters if args.workload == "bve_n1024" else 0)
     clk = clocks.stop()
     out = {"metric": METRIC, "value": r["value"], "unit": "HVP/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -383,6 +422,8 @@ def bve_arm(args):
            "clocks": clk}
     if "gn_step" in r:
         out["gn_step"] = r["gn_step"]
+    if "gn_iterations" in r:
+        out["gn_iterations"] = r["gn_iterations"]
     print(json.dumps(out), flush=True)
 
 
@@ -666,11 +707,17 @@ def gyre_arm(args):
 
 
 def measured_hbm_gbs():
+    return hbm_peak()[0]
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of MEASURED_PEAKS.json, else
+    the 6.8 TB/s fallback of an earlier measurement on a GB300."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
     except (OSError, KeyError, ValueError):
-        return 6800.0
+        return 6800.0, "fallback 6800 GB/s (MEASURED_PEAKS.json absent; of fallback)"
 
 
 def gpu_arm(args):
