@@ -405,12 +405,12 @@ static int host_scalar(Prob* P, double* out, cudaStream_t st) {
 // ------------------------------------------------------------------ sketch helpers
 // Workspace for the dense steps of one sketch.
 struct SketchWS {
-  Buf a, b, c, g, g2, u, w, info, jw;
+  Buf a, b, c, g, g2, u, w, info, jw, tc;
   int64_t* shifted = nullptr;  // problem counter of shifted CholeskyQR retries
   int tall = kTall3xTF32;      // arithmetic of the FP32 tall products (sketch_opts.gemm)
   void release() {
     a.release(); b.release(); c.release(); g.release(); g2.release(); u.release(); w.release();
-    info.release(); jw.release();
+    info.release(); jw.release(); tc.release();
   }
 };
 
@@ -418,11 +418,13 @@ struct SketchWS {
 // columns go to the tensor cores in the sketch's mode (or the CUDA-core kernel
 // when asked); FP64 operands and single vectors keep the FP64 / CUDA-core path.
 template <typename T, typename TC>
-static int tall_nn(const SketchWS& ws, int rows, int kk, int c, double alpha, const T* A, int lda,
+static int tall_nn(SketchWS& ws, int rows, int kk, int c, double alpha, const T* A, int lda,
                    const double* B, int ldb, int transB, double beta, TC* C, int ldc, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
-    if (c > 1 && kk > 0 && ws.tall != kTallSIMT)
-      return tall_gemm_tc<TC>(ws.tall, rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, st);
+    if (c > 1 && kk > 0 && ws.tall != kTallSIMT) {
+      SC4_TRY(ws.tc.ensure(tall_pack_bytes(ws.tall, kk, c)));
+      return tall_gemm_tc<TC>(ws.tall, rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, ws.tc.p, st);
+    }
   }
   return gemm_nn<T, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, st);
 }
@@ -1629,6 +1631,7 @@ int sc4dvar_tall_gemm(int mode, int rows, int kk, int c, double alpha, const flo
   else
     SC4_TRY(tall_nn<float, float>(ws, rows, kk, c, alpha, A, lda, B, ldb, transB, beta, (float*)C, ldc, st));
   SC4_CUDA(cudaStreamSynchronize(st));
+  ws.release();
   return tall_tc_take_error();
 }
 

@@ -13,8 +13,10 @@
 // tensor memory (N, rounded up to a power of two, of the 512 TMEM columns of the
 // SM). K runs in chunks of 16 through two shared-memory stages: while the tensor
 // core multiplies one chunk (issued by one thread, completion signalled on an
-// mbarrier by tcgen05.commit), the four warps load the next into registers, then
-// convert and stage it. Operands sit in shared memory in
+// mbarrier by tcgen05.commit), the four warps load the next chunk of A into
+// registers, then convert and stage it. The small factor is converted once per
+// product by a packing kernel into the operand format of every stage, and each
+// stage's B chunk arrives by a bulk copy of the tensor-memory-access engine. Operands sit in shared memory in
 // the canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
 // adjacent in K at LBO = (tile rows / 8) x 128 bytes, adjacent in rows at
 // SBO = 128 bytes. The epilogue reads the accumulator with tcgen05.ld (warp w
@@ -116,16 +118,41 @@ __device__ __forceinline__ void put_row(unsigned char* dst, int split_bytes, con
   }
 }
 
+// The small factor converted once into the operand format, chunk by chunk, for
+// every column tile: block (y, ch) holds NSPLIT x b_bytes(Nt_y) bytes laid out
+// exactly as a stage's B region, so a CTA fetches it with one bulk copy.
+template <int MODE>
+__global__ void tall_pack_b_kernel(int kk, int c, const double* __restrict__ B, int ldb, int transB, int ntl,
+                                   int nch, unsigned char* __restrict__ out) {
+  using Md = TallMode<MODE>;
+  constexpr int T = Md::T;
+  const int y = blockIdx.y, ch = blockIdx.x;
+  const int c0 = y * kNmax, Nt = min(ntl, (c - c0 + 15) / 16 * 16);
+  const int bB = Md::b_bytes(Nt);
+  unsigned char* dst = out + ((size_t)y * nch + ch) * Md::NSPLIT * Md::b_bytes(ntl);
+  const int k0 = ch * kKC;
+  for (int e = threadIdx.x; e < Nt * (kKC / T); e += blockDim.x) {
+    const int n = e % Nt, q = e / Nt, j = c0 + n;
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+      const int k = k0 + q * T + i;
+      v[i] = (j < c && k < kk) ? (float)(transB ? B[(size_t)k * ldb + j] : B[(size_t)j * ldb + k]) : 0.f;
+    }
+    put_row<MODE>(dst + (q * (Nt / 8) + (n >> 3)) * 128 + (n & 7) * 16, bB, v);
+  }
+}
+
 // One CTA: rows r0 .. r0 + 127 and columns c0 .. c0 + Nt - 1 (Nt <= ntl, the
 // widest tile of the launch, which sizes the shared stages; tcols TMEM columns).
-// Thread t stages row t of A and rows t, t + 128 of the B operand; the next
-// chunk's values are loaded into registers while the tensor core multiplies.
+// Thread t stages row t of A (the next chunk's values are loaded into registers
+// while the tensor core multiplies); thread 0 brings the chunk of the packed B
+// operand with a bulk copy (cp.async.bulk) that completes the stage's B barrier.
 template <int MODE, typename TC>
 __global__ void __launch_bounds__(128) tall_tc_kernel(int rows, int kk, int c, float alpha,
                                                       const float* __restrict__ A, int lda,
-                                                      const double* __restrict__ B, int ldb, int transB,
-                                                      double beta, TC* __restrict__ C, int ldc, int ntl,
-                                                      int tcols) {
+                                                      const unsigned char* __restrict__ Bpk, double beta,
+                                                      TC* __restrict__ C, int ldc, int ntl, int tcols) {
   using Md = TallMode<MODE>;
   constexpr int T = Md::T;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -134,16 +161,15 @@ __global__ void __launch_bounds__(128) tall_tc_kernel(int rows, int kk, int c, f
   const int Nt = min(ntl, (c - c0 + 15) / 16 * 16);
   const int bB = Md::b_bytes(Nt);
   const int stage = Md::stage_bytes(ntl);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * stage);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * stage);  // [0, 1] products done, [2, 3] B landed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 4);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
                  "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar + 1)));
+    for (int b = 0; b < 4; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar + b)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -153,21 +179,14 @@ __global__ void __launch_bounds__(128) tall_tc_kernel(int rows, int kk, int c, f
   const uint32_t idesc = instr_desc(MODE == kTallBF16 ? 1 : 2, 128, Nt);
   const int nch = (kk + kKC - 1) / kKC;
   const int gr = r0 + tid;
-  float va[kKC], vb[2][kKC];
+  const unsigned char* bsrc = Bpk + (size_t)blockIdx.y * nch * Md::NSPLIT * Md::b_bytes(ntl);
+  const uint32_t bbytes = Md::NSPLIT * bB;
+  float va[kKC];
   auto load = [&](int ch) {
     const int k0 = ch * kKC;
 #pragma unroll
     for (int k = 0; k < kKC; ++k)
       va[k] = (gr < rows && k0 + k < kk) ? A[(size_t)(k0 + k) * lda + gr] : 0.f;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int n = tid + 128 * h, j = c0 + n;
-      const bool in = n < Nt && j < c;
-#pragma unroll
-      for (int k = 0; k < kKC; ++k)
-        vb[h][k] = (in && k0 + k < kk) ? (float)(transB ? B[(size_t)(k0 + k) * ldb + j] : B[(size_t)j * ldb + k0 + k])
-                                       : 0.f;
-    }
   };
   bool ok = true;
   int issued = -1;  // last chunk whose products were committed
@@ -185,17 +204,23 @@ __global__ void __launch_bounds__(128) tall_tc_kernel(int rows, int kk, int c, f
     }
     unsigned char* As = smem + s * stage;
     unsigned char* Bs = As + Md::kAStage;
-#pragma unroll
-    for (int q = 0; q < kKC / T; ++q) {
-      put_row<MODE>(As + (q * 16 + (tid >> 3)) * 128 + (tid & 7) * 16, Md::kABytes, va + q * T);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int n = tid + 128 * h;
-        if (n < Nt) put_row<MODE>(Bs + (q * (Nt / 8) + (n >> 3)) * 128 + (n & 7) * 16, bB, vb[h] + q * T);
-      }
+    if (tid == 0) {
+      // the packed B chunk by a bulk copy (TMA) completing the stage's B barrier
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar + 2 + s)),
+                   "r"(bbytes)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              saddr(Bs)),
+          "l"(bsrc + (size_t)ch * Md::NSPLIT * Md::b_bytes(ntl)), "r"(bbytes), "r"(saddr(bar + 2 + s))
+          : "memory");
     }
+#pragma unroll
+    for (int q = 0; q < kKC / T; ++q)
+      put_row<MODE>(As + (q * 16 + (tid >> 3)) * 128 + (tid & 7) * 16, Md::kABytes, va + q * T);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (tid == 0 && !mbar_wait(saddr(bar + 2 + s), (ch >> 1) & 1)) atomicExch(&g_tall_err, 1);
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t a0 = saddr(As), b0 = saddr(Bs);
@@ -266,35 +291,57 @@ __global__ void __launch_bounds__(128) tall_tc_kernel(int rows, int kk, int c, f
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
+template <int MODE>
+size_t pack_bytes(int kk, int c) {
+  const int ntl = std::min(kNmax, (c + 15) / 16 * 16);
+  const size_t nch = (size_t)(kk + kKC - 1) / kKC, ny = (size_t)(c + kNmax - 1) / kNmax;
+  return ny * nch * TallMode<MODE>::NSPLIT * TallMode<MODE>::b_bytes(ntl);
+}
+
 template <int MODE, typename TC>
 int launch_tall(int rows, int kk, int c, double alpha, const float* A, int lda, const double* B, int ldb,
-                int transB, double beta, TC* C, int ldc, cudaStream_t st) {
+                int transB, double beta, TC* C, int ldc, void* pack, cudaStream_t st) {
   const int ntl = std::min(kNmax, (c + 15) / 16 * 16);
+  const int nch = (kk + kKC - 1) / kKC;
   int tcols = 32;
   while (tcols < ntl) tcols *= 2;
+  dim3 pgrid(nch, div_up(c, kNmax));
+  tall_pack_b_kernel<MODE><<<pgrid, 256, 0, st>>>(kk, c, B, ldb, transB, ntl, nch,
+                                                 static_cast<unsigned char*>(pack));
+  SC4_LAUNCH_CHECK();
   const int smem = TallMode<MODE>::smem_bytes(ntl);
   auto kern = tall_tc_kernel<MODE, TC>;
   SC4_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   dim3 grid(div_up(rows, 128), div_up(c, kNmax));
-  kern<<<grid, 128, smem, st>>>(rows, kk, c, (float)alpha, A, lda, B, ldb, transB, beta, C, ldc, ntl, tcols);
+  kern<<<grid, 128, smem, st>>>(rows, kk, c, (float)alpha, A, lda, static_cast<const unsigned char*>(pack), beta,
+                                C, ldc, ntl, tcols);
   SC4_LAUNCH_CHECK();
   return SC4DVAR_OK;
 }
 
 }  // namespace
 
+size_t tall_pack_bytes(int mode, int kk, int c) {
+  if (kk <= 0 || c <= 0) return 0;
+  switch (mode) {
+    case kTallTF32: return pack_bytes<kTallTF32>(kk, c);
+    case kTallBF16: return pack_bytes<kTallBF16>(kk, c);
+    default: return pack_bytes<kTall3xTF32>(kk, c);
+  }
+}
+
 template <typename TC>
 int tall_gemm_tc(int mode, int rows, int kk, int c, double alpha, const float* A, int lda, const double* B,
-                 int ldb, int transB, double beta, TC* C, int ldc, cudaStream_t st) {
+                 int ldb, int transB, double beta, TC* C, int ldc, void* pack, cudaStream_t st) {
   if (rows <= 0 || c <= 0) return SC4DVAR_OK;
   if (kk <= 0) return gemm_nn<float, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, st);
   switch (mode) {
     case kTallTF32:
-      return launch_tall<kTallTF32, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, st);
+      return launch_tall<kTallTF32, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, pack, st);
     case kTallBF16:
-      return launch_tall<kTallBF16, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, st);
+      return launch_tall<kTallBF16, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, pack, st);
     default:
-      return launch_tall<kTall3xTF32, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, st);
+      return launch_tall<kTall3xTF32, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, pack, st);
   }
 }
 
@@ -311,8 +358,8 @@ int tall_tc_take_error() {
 }
 
 template int tall_gemm_tc<float>(int, int, int, int, double, const float*, int, const double*, int, int, double,
-                                 float*, int, cudaStream_t);
+                                 float*, int, void*, cudaStream_t);
 template int tall_gemm_tc<double>(int, int, int, int, double, const float*, int, const double*, int, int,
-                                  double, double*, int, cudaStream_t);
+                                  double, double*, int, void*, cudaStream_t);
 
 }  // namespace sc4

@@ -7,9 +7,11 @@ enum { kTall3xTF32 = 0, kTallSIMT = 1, kTallTF32 = 2, kTallBF16 = 3 };
 
 // C (rows x c) = alpha A op(B) + beta C on the tensor cores; A FP32 column-major
 // (rows x kk), B FP64 (kk x c, or c x kk with transB), C FP32 or FP64.
+// pack: device workspace of tall_pack_bytes(mode, kk, c) bytes for the converted B.
+size_t tall_pack_bytes(int mode, int kk, int c);
 template <typename TC>
 int tall_gemm_tc(int mode, int rows, int kk, int c, double alpha, const float* A, int lda, const double* B,
-                 int ldb, int transB, double beta, TC* C, int ldc, cudaStream_t st);
+                 int ldb, int transB, double beta, TC* C, int ldc, void* pack, cudaStream_t st);
 // SC4DVAR_ERR_TIMEOUT (and clears it) if a tensor-core wait gave up since the last
 // call; synchronizes with the device.
 int tall_tc_take_error();
