@@ -1412,6 +1412,7 @@ int sc4dvar_problem_create(const sc4dvar_problem_desc* d, sc4dvar_problem_t* out
     g.Fy = reinterpret_cast<double*>(b + nn * 8 + 2 * f * 8);
     char* b4 = b + nn * 8 + 2 * f * 8 + (size_t)g.ny * 8;
     g.S32 = reinterpret_cast<float*>(b4);
+    g.S_tc = g.nx == 128 ? static_cast<void*>(b + gyre_tc_offset(g.nx)) : nullptr;
     g.pois32 = reinterpret_cast<float*>(b4 + nn * 4);
     g.prior32 = reinterpret_cast<float*>(b4 + nn * 4 + f * 4);
     char* sb = static_cast<char*>(P->gy_stages);

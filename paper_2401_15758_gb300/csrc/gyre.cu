@@ -29,6 +29,7 @@
 #include <vector>
 #include "common.cuh"
 #include "gyre.cuh"
+#include "tall_tc.cuh"
 
 namespace sc4 {
 namespace {
@@ -175,137 +176,9 @@ __global__ void __launch_bounds__(kTileThreads) gy_dst_tiled_kernel(int nx, int 
 }
 
 // Tensor-core form for FP32 fields with nx = 128 (the row transform is a dense
-// rows x 128 by 128 x 128 product): mma.sync m16n8k8 TF32 in the split form of
-// Ootomo & Yokota (2022), a = a_hi + a_lo with a_hi = tf32(a), a_lo =
-// tf32(a - a_hi), and a b ~ a_lo b_hi + a_hi b_lo + a_hi b_hi accumulated in
-// FP32 (the dropped a_lo b_lo is below FP32 rounding), which keeps FP32
-// accuracy. A persistent CTA holds S in shared memory and walks tiles of 128
-// rows, the next tile arriving by asynchronous copies into the second buffer
-// while the current one is multiplied; 16 warps, each a 32 x 32 block of the
-// 128 x 128 output tile, the three products of a k-step issued as three passes
-// over the 8 independent accumulator tiles. Row strides are padded (132 and
-// 136 words) so the fragment reads of a warp hit 32 distinct banks.
-constexpr int kTcN = 128, kTcLdA = 132, kTcLdB = 136;
-
-size_t tc_smem() { return (2 * (size_t)kTcN * kTcLdA + (size_t)kTcN * kTcLdB) * 4; }
-
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// rows r0 .. r0+127 of the input into a padded tile; rows past the end read as
-// zero (source size 0)
-__device__ __forceinline__ void tc_load_tile(float* dst, const float* __restrict__ in, int ldi, int ny,
-                                             int rows, int r0) {
-  for (int e = threadIdx.x; e < kTcN * (kTcN / 4); e += blockDim.x) {
-    const int rr = e >> 5, q = e & 31, r = r0 + rr;
-    const float* src = in;
-    int bytes = 0;
-    if (r < rows) {
-      const int c = r / ny, j = r - c * ny;
-      src = in + (size_t)c * ldi + (size_t)j * kTcN + 4 * q;
-      bytes = 16;
-    }
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst + rr * kTcLdA + 4 * q);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
-  }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-__global__ void __launch_bounds__(512, 1) gy_dst_tf32x3_kernel(int ny, int rows, const float* __restrict__ in,
-                                                               int ldi, const float* __restrict__ Sm,
-                                                               float* __restrict__ out, int ldo) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float* sA = reinterpret_cast<float*>(smraw);  // [2][128][kTcLdA] input tiles
-  float* sB = sA + 2 * kTcN * kTcLdA;           // [128][kTcLdB] S
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int wm = warp >> 2, wn = warp & 3;  // warp block: rows 32 wm.., columns 32 wn..
-  const int tiles = (rows + kTcN - 1) / kTcN;
-  if ((int)blockIdx.x < tiles) tc_load_tile(sA, in, ldi, ny, rows, blockIdx.x * kTcN);
-  for (int e = tid; e < kTcN * kTcN; e += blockDim.x) sB[(e >> 7) * kTcLdB + (e & 127)] = Sm[e];
-  int it = 0;
-  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
-    const float* cA = sA + (it & 1) * kTcN * kTcLdA;
-    const int nxt = tile + gridDim.x;
-    if (nxt < tiles) {
-      tc_load_tile(sA + ((it + 1) & 1) * kTcN * kTcLdA, in, ldi, ny, rows, nxt * kTcN);
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    }
-    __syncthreads();  // this tile (and S) visible to every warp
-    float acc[2][4][4];
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[mi][ni][q] = 0.f;
-#pragma unroll 1
-    for (int k0 = 0; k0 < kTcN; k0 += 8) {
-      uint32_t bh[4][2], bl[4][2], ah[2][4], al[2][4];
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni) {
-        const int col = wn * 32 + ni * 8 + g;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float v = sB[(k0 + t + 4 * h) * kTcLdB + col];
-          bh[ni][h] = tf32_rna(v);
-          bl[ni][h] = tf32_rna(v - __uint_as_float(bh[ni][h]));
-        }
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const float* a0p = cA + (wm * 32 + mi * 16 + g) * kTcLdA + k0 + t;
-        const float x[4] = {a0p[0], a0p[8 * kTcLdA], a0p[4], a0p[8 * kTcLdA + 4]};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          ah[mi][q] = tf32_rna(x[q]);
-          al[mi][q] = tf32_rna(x[q] - __uint_as_float(ah[mi][q]));
-        }
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_tf32(acc[mi][ni], al[mi], bh[ni]);
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_tf32(acc[mi][ni], ah[mi], bl[ni]);
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_tf32(acc[mi][ni], ah[mi], bh[ni]);
-    }
-    const int r0 = tile * kTcN;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = r0 + wm * 32 + mi * 16 + g + 8 * h;
-        if (r >= rows) continue;
-        const int c = r / ny, j = r - c * ny;
-        float* orow = out + (size_t)c * ldo + (size_t)j * kTcN;
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) {
-          const int col = wn * 32 + ni * 8 + 2 * t;
-          orow[col] = acc[mi][ni][2 * h];
-          orow[col + 1] = acc[mi][ni][2 * h + 1];
-        }
-      }
-    __syncthreads();  // every warp done with this buffer before it is refilled
-  }
-}
+// rows x 128 by 128 x 128 product): rows128_tc in tall_tc.cu, tcgen05 MMAs in
+// the 3xTF32 split with the accumulators in tensor memory and S packed once at
+// set-up (GyreGeom::S_tc).
 
 size_t tiled_smem(int nx, size_t tb) {
   const int CG = nx / 8, BR = 4 * (kTileThreads / CG);
@@ -321,15 +194,10 @@ int dst_rows(const GyreGeom& g, int k, const TI* in, int ldi, const TC* Sm, TO* 
                 std::is_same<TO, float>::value) {
     // tensor-core form: nx = 128, no added term, 16-byte aligned input rows,
     // at least 16 tiles of 128 rows
-    const int tiles = div_up(rows, kTcN);
-    if (nx == kTcN && Z == nullptr && ((uintptr_t)in % 16) == 0 && ldi % 4 == 0 && tiles >= 16) {
-      const size_t smem = tc_smem();
-      SC4_CUDA(cudaFuncSetAttribute(gy_dst_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-      gy_dst_tf32x3_kernel<<<std::min(tiles, 152), 512, smem, st>>>(g.ny, rows, in, ldi, Sm, out, ldo);
-      SC4_LAUNCH_CHECK();
-      return SC4DVAR_OK;
-    }
+    const int tiles = div_up(rows, 128);
+    if (nx == 128 && g.S_tc && Z == nullptr && ((uintptr_t)in % 16) == 0 && ldi % 4 == 0 &&
+        ((uintptr_t)out % 16) == 0 && ldo % 4 == 0 && tiles >= 16)
+      return rows128_tc(g.ny, rows, in, ldi, g.S_tc, out, ldo, st);
   }
   const int BR = 4 * (kTileThreads / std::max(1, nx / 8));
   if (nx >= 16 && div_up(rows, BR) >= 152) {
@@ -676,7 +544,14 @@ void thomas_factors(int nx, int ny, double alpha, double beta, std::vector<doubl
 size_t gyre_setup_bytes(int nx) {
   const int ny = 2 * nx + 1;
   const size_t nn = (size_t)nx * nx, f = 2 * (size_t)nx * ny;
-  return nn * (8 + 4) + 2 * f * (8 + 4) + (size_t)ny * 8;
+  const size_t base = nn * (8 + 4) + 2 * f * (8 + 4) + (size_t)ny * 8;
+  return nx == 128 ? gyre_tc_offset(nx) + rows128_pack_bytes() : base;
+}
+
+size_t gyre_tc_offset(int nx) {
+  const int ny = 2 * nx + 1;
+  const size_t nn = (size_t)nx * nx, f = 2 * (size_t)nx * ny;
+  return (nn * (8 + 4) + 2 * f * (8 + 4) + (size_t)ny * 8 + 255) & ~(size_t)255;
 }
 
 size_t gyre_stage_bytes(int nx, int N, int S) {
@@ -711,6 +586,7 @@ int gyre_setup(GyreGeom& g, double prior_a, double prior_b, cudaStream_t st) {
   SC4_CUDA(cudaMemcpyAsync(g.prior64, prior.data(), prior.size() * 8, cudaMemcpyHostToDevice, st));
   SC4_CUDA(cudaMemcpyAsync(g.prior32, prior32.data(), prior32.size() * 4, cudaMemcpyHostToDevice, st));
   SC4_CUDA(cudaMemcpyAsync(g.Fy, Fy.data(), Fy.size() * 8, cudaMemcpyHostToDevice, st));
+  if (g.S_tc) SC4_TRY(rows128_pack(g.S32, g.S_tc, st));
   SC4_CUDA(cudaStreamSynchronize(st));
   return SC4DVAR_OK;
 }

@@ -29,6 +29,7 @@ struct GyreGeom {
   // [2][ny][nx]: inverse pivots, then c'_j = off * pivot^{-1}
   double* S64;
   float* S32;
+  void* S_tc;                  // nx = 128: S packed for the tensor-core row transform (else null)
   double* pois64;
   float* pois32;
   double pois_off;             // off-diagonal of the Poisson systems (-1/h^2)
@@ -46,6 +47,8 @@ struct GyreGeom {
 // Device bytes of the set-up arrays (transform, factors, forcing) and of the
 // stage states.
 size_t gyre_setup_bytes(int nx);
+// offset of the packed transform (S_tc) in the set-up block (nx = 128)
+size_t gyre_tc_offset(int nx);
 size_t gyre_stage_bytes(int nx, int N, int S);
 // Fills S, the factors and the forcing; the pointers must already be set.
 int gyre_setup(GyreGeom& g, double prior_a, double prior_b, cudaStream_t st);

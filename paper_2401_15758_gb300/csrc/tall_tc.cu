@@ -121,8 +121,8 @@ __device__ __forceinline__ void put_row(unsigned char* dst, int split_bytes, con
 // The small factor converted once into the operand format, chunk by chunk, for
 // every column tile: block (y, ch) holds NSPLIT x b_bytes(Nt_y) bytes laid out
 // exactly as a stage's B region, so a CTA fetches it with one bulk copy.
-template <int MODE>
-__global__ void tall_pack_b_kernel(int kk, int c, const double* __restrict__ B, int ldb, int transB, int ntl,
+template <int MODE, typename TB>
+__global__ void tall_pack_b_kernel(int kk, int c, const TB* __restrict__ B, int ldb, int transB, int ntl,
                                    int nch, unsigned char* __restrict__ out) {
   using Md = TallMode<MODE>;
   constexpr int T = Md::T;
@@ -306,8 +306,8 @@ int launch_tall(int rows, int kk, int c, double alpha, const float* A, int lda, 
   int tcols = 32;
   while (tcols < ntl) tcols *= 2;
   dim3 pgrid(nch, div_up(c, kNmax));
-  tall_pack_b_kernel<MODE><<<pgrid, 256, 0, st>>>(kk, c, B, ldb, transB, ntl, nch,
-                                                 static_cast<unsigned char*>(pack));
+  tall_pack_b_kernel<MODE, double><<<pgrid, 256, 0, st>>>(kk, c, B, ldb, transB, ntl, nch,
+                                                         static_cast<unsigned char*>(pack));
   SC4_LAUNCH_CHECK();
   const int smem = TallMode<MODE>::smem_bytes(ntl);
   auto kern = tall_tc_kernel<MODE, TC>;
@@ -317,6 +317,165 @@ int launch_tall(int rows, int kk, int c, double alpha, const float* A, int lda, 
                                 C, ldc, ntl, tcols);
   SC4_LAUNCH_CHECK();
   return SC4DVAR_OK;
+}
+
+// ---------------------------------------------------------------- 128-point row transform
+// out[r][p] = sum_i in[r][i] S[i][p] for rows r = c ny + j of k fields (row r at
+// in + c ldi + j 128), S a fixed 128 x 128 FP32 matrix packed once
+// (tall_pack_factor) in the staged operand format of all eight 16-wide K chunks
+// (128 KB for the 3xTF32 split). A persistent CTA keeps the whole packed S in
+// shared memory (one bulk copy at start) and walks 128-row tiles: per tile,
+// eight K chunks of the rows go through two shared stages, each followed by six
+// tcgen05 MMAs (two K steps of 8, three TF32 products each) into a 128-column
+// TMEM accumulator; the epilogue writes every row's 128 outputs with vector stores.
+constexpr int kRowN = 128;
+constexpr int kRowChunks = kRowN / kKC;
+
+__global__ void __launch_bounds__(128, 1) rows128_tc_kernel(int ny, int rows, const float* __restrict__ in, int ldi,
+                                                            const unsigned char* __restrict__ Spk,
+                                                            float* __restrict__ out, int ldo) {
+  using Md = TallMode<kTall3xTF32>;
+  constexpr int T = Md::T;
+  constexpr int kBChunk = Md::NSPLIT * ((kKC / T) * (kRowN / 8) * 128);  // 16 KB
+  constexpr int kBAll = kRowChunks * kBChunk;                             // 128 KB
+  const int bB = Md::b_bytes(kRowN);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* Bsm = smem;
+  unsigned char* Ast = smem + kBAll;                                      // [2][kAStage]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Ast + 2 * Md::kAStage);     // [0, 1] products, [2] S landed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                 "r"(2 * kRowN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar + b)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar + 2)), "r"(kBAll)
+                 : "memory");
+    for (int ch = 0; ch < kRowChunks; ++ch)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              saddr(Bsm + ch * kBChunk)),
+          "l"(Spk + (size_t)ch * kBChunk), "r"(kBChunk), "r"(saddr(bar + 2))
+          : "memory");
+  }
+  const uint32_t idesc = instr_desc(2, 128, kRowN);
+  const int tiles = (rows + 127) / 128;
+  bool ok = true, have_s = false;
+  int g = 0;  // chunks staged by this CTA so far
+  for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    const int r = tile * 128 + tid;
+    const bool valid = r < rows;
+    const int c = valid ? r / ny : 0, j = valid ? r - c * ny : 0;
+    const float* rin = in + (size_t)c * ldi + (size_t)j * kRowN;
+    for (int ch = 0; ch < kRowChunks; ++ch, ++g) {
+      const int s = g & 1;
+      if (g >= 2) {
+        const bool w = mbar_wait(saddr(bar + s), ((g - 2) >> 1) & 1);
+        if (!__syncthreads_and(w)) {
+          ok = false;
+          break;
+        }
+      }
+      float v[kKC];
+      if (valid) {
+#pragma unroll
+        for (int q = 0; q < kKC / 4; ++q) {
+          const float4 x = *reinterpret_cast<const float4*>(rin + ch * kKC + 4 * q);
+          v[4 * q] = x.x;
+          v[4 * q + 1] = x.y;
+          v[4 * q + 2] = x.z;
+          v[4 * q + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kKC; ++k) v[k] = 0.f;
+      }
+      unsigned char* As = Ast + s * Md::kAStage;
+#pragma unroll
+      for (int q = 0; q < kKC / T; ++q)
+        put_row<kTall3xTF32>(As + (q * 16 + (tid >> 3)) * 128 + (tid & 7) * 16, Md::kABytes, v + q * T);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        if (!have_s) {
+          if (!mbar_wait(saddr(bar + 2), 0)) atomicExch(&g_tall_err, 1);
+          have_s = true;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = saddr(As), b0 = saddr(Bsm + ch * kBChunk);
+#pragma unroll
+        for (int ki = 0; ki < kKC / Md::KI; ++ki) {
+          const int q = ki * (Md::KI / T);
+#pragma unroll
+          for (int tm = 0; tm < 3; ++tm) {
+            // hi hi into columns 0..127; the two correction products hi lo and
+            // lo hi into columns 128..255, summed with the first in the epilogue
+            const int sa = (tm == 2) ? 1 : 0, sb = (tm == 1) ? 1 : 0;
+            const uint64_t ad = smem_desc(a0 + sa * Md::kABytes + q * 16 * 128, 16 * 128, 128);
+            const uint64_t bd = smem_desc(b0 + sb * bB + q * (kRowN / 8) * 128, (kRowN / 8) * 128, 128);
+            const uint32_t acc = (ch > 0 || ki > 0 || tm == 2) ? 1u : 0u;
+            const uint32_t dst = tmem + (tm > 0 ? (uint32_t)kRowN : 0u);
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         saddr(bar + s))
+                     : "memory");
+      }
+    }
+    if (!ok) break;
+    // the tile's products are done: read the accumulator row by row
+    const bool w = mbar_wait(saddr(bar + ((g - 1) & 1)), ((g - 1) >> 1) & 1);
+    if (!__syncthreads_and(w)) {
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    float* rout = out + (size_t)c * ldo + (size_t)j * kRowN;
+    for (int cb = 0; cb < kRowN; cb += 8) {
+      uint32_t x[8], y[8];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
+                     "=r"(x[7])
+                   : "r"(ta));
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]),
+                     "=r"(y[7])
+                   : "r"(ta + (uint32_t)kRowN));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) o[i] = __uint_as_float(x[i]) + __uint_as_float(y[i]);
+      if (valid) {
+        *reinterpret_cast<float4*>(rout + cb) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4*>(rout + cb + 4) = make_float4(o[4], o[5], o[6], o[7]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // every warp has read the accumulator before the next tile overwrites it
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_tall_err, 1);
+    if (g > 0) mbar_wait(saddr(bar + ((g - 1) & 1)), ((g - 1) >> 1) & 1);  // products already issued
+  }
+  if (tid == 0 && !have_s) mbar_wait(saddr(bar + 2), 0);  // the copy of S has landed
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kRowN));
 }
 
 }  // namespace
@@ -343,6 +502,26 @@ int tall_gemm_tc(int mode, int rows, int kk, int c, double alpha, const float* A
     default:
       return launch_tall<kTall3xTF32, TC>(rows, kk, c, alpha, A, lda, B, ldb, transB, beta, C, ldc, pack, st);
   }
+}
+
+size_t rows128_pack_bytes() { return (size_t)kRowChunks * 2 * (kKC / 4) * (kRowN / 8) * 128; }
+
+int rows128_pack(const float* S, void* out, cudaStream_t st) {
+  tall_pack_b_kernel<kTall3xTF32, float><<<dim3(kRowChunks, 1), 256, 0, st>>>(
+      kRowN, kRowN, S, kRowN, 1, kRowN, kRowChunks, static_cast<unsigned char*>(out));
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
+}
+
+int rows128_tc(int ny, int rows, const float* in, int ldi, const void* Spk, float* out, int ldo, cudaStream_t st) {
+  if (rows <= 0) return SC4DVAR_OK;
+  const int smem = (int)rows128_pack_bytes() + 2 * TallMode<kTall3xTF32>::kAStage + 64;
+  SC4_CUDA(cudaFuncSetAttribute(rows128_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int tiles = div_up(rows, 128);
+  rows128_tc_kernel<<<std::min(tiles, 152), 128, smem, st>>>(ny, rows, in, ldi,
+                                                            static_cast<const unsigned char*>(Spk), out, ldo);
+  SC4_LAUNCH_CHECK();
+  return SC4DVAR_OK;
 }
 
 int tall_tc_take_error() {
