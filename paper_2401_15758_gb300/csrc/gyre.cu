@@ -192,12 +192,13 @@ int dst_rows(const GyreGeom& g, int k, const TI* in, int ldi, const TC* Sm, TO* 
   if (rows <= 0) return SC4DVAR_OK;
   if constexpr (std::is_same<TI, float>::value && std::is_same<TC, float>::value &&
                 std::is_same<TO, float>::value) {
-    // tensor-core form: nx = 128, no added term, 16-byte aligned input rows,
-    // at least 16 tiles of 128 rows
+    // tensor-core form: nx = 128, no added term, input fields back to back from
+    // a 16-byte aligned start (one 2D tensor map over all rows), 16-byte aligned
+    // output rows, at least 16 tiles of 128 rows
     const int tiles = div_up(rows, 128);
-    if (nx == 128 && g.S_tc && Z == nullptr && ((uintptr_t)in % 16) == 0 && ldi % 4 == 0 &&
+    if (nx == 128 && g.S_tc && Z == nullptr && ((uintptr_t)in % 16) == 0 && ldi == g.ny * nx &&
         ((uintptr_t)out % 16) == 0 && ldo % 4 == 0 && tiles >= 16)
-      return rows128_tc(g.ny, rows, in, ldi, g.S_tc, out, ldo, st);
+      return rows128_tc(g.ny, rows, in, g.S_tc, out, ldo, st);
   }
   const int BR = 4 * (kTileThreads / std::max(1, nx / 8));
   if (nx >= 16 && div_up(rows, BR) >= 152) {

@@ -33,6 +33,8 @@
 // word (reported as SC4DVAR_ERR_TIMEOUT by the next synchronizing call), waits a
 // bounded time for the products already issued, frees its tensor memory and
 // returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cstdint>
@@ -267,11 +269,14 @@ __global__ void __launch_bounds__(128) tall_tc_kernel(int rows, int kk, int c, f
     for (int cb = 0; cb < Nt; cb += 8) {
       uint32_t v[8];
       const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                     "=r"(v[7])
-                   : "r"(ta));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      // load and wait in one statement: the registers are defined only once
+      // the wait has retired the load
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+          "tcgen05.wait::ld.sync.aligned;"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+          : "r"(ta)
+          : "memory");
       if (row < rows) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -320,162 +325,299 @@ int launch_tall(int rows, int kk, int c, double alpha, const float* A, int lda, 
 }
 
 // ---------------------------------------------------------------- 128-point row transform
-// out[r][p] = sum_i in[r][i] S[i][p] for rows r = c ny + j of k fields (row r at
-// in + c ldi + j 128), S a fixed 128 x 128 FP32 matrix packed once
-// (tall_pack_factor) in the staged operand format of all eight 16-wide K chunks
-// (128 KB for the 3xTF32 split). A persistent CTA keeps the whole packed S in
-// shared memory (one bulk copy at start) and walks 128-row tiles: per tile,
-// eight K chunks of the rows go through two shared stages, each followed by six
-// tcgen05 MMAs (two K steps of 8, three TF32 products each) into a 128-column
-// TMEM accumulator; the epilogue writes every row's 128 outputs with vector stores.
+// out[r][p] = sum_i in[r][i] S[i][p] for the rows r = c ny + j of k fields held
+// back to back (row r at in + 128 r; its output at out + c ldo + 128 j), S a
+// fixed 128 x 128 FP32 matrix packed once (rows128_pack) in the staged operand
+// format of its eight 16-wide K chunks (128 KB for the 3xTF32 split). A
+// persistent CTA keeps the packed S in shared memory and walks 128-row tiles
+// with four roles that run ahead of one another through mbarrier rings (every
+// wait bounded, its verdict made uniform across the warp):
+//   warp 8 (one thread)  tensor-memory-access loads of the raw FP32 K chunks of
+//                        the rows (2D tensor map, box 16 x 128) into a ring of
+//                        kRawSlots slots;
+//   warps 0-3            split each chunk into TF32 hi and lo parts in the
+//                        canonical K-major operand layout (kAStages stages);
+//   warp 9 (one thread)  six tcgen05 MMAs per chunk: hi hi into accumulator
+//                        columns 0..127, hi lo and lo hi into 128..255 (summed
+//                        in the epilogue), two such accumulators (all 512 TMEM
+//                        columns) so that one tile's products overlap the
+//                        previous tile's epilogue;
+//   warps 4-7            read an accumulator with tcgen05.ld (warp 4 + w owns
+//                        TMEM lanes 32w .. 32w + 31), add its two halves and
+//                        write the rows through a per-warp shared slab of 32
+//                        columns, so that every store instruction covers four
+//                        128-byte row segments.
 constexpr int kRowN = 128;
 constexpr int kRowChunks = kRowN / kKC;
+constexpr int kRawSlots = 4;
+constexpr int kAStages = 3;
+constexpr int kRawBytes = kKC * kRowN * 4;  // 16 floats of 128 rows
+constexpr int kRowThreads = 320;
+constexpr int kSlabStride = 36;             // floats per slab row (16-byte rows, no bank conflicts)
 
-__global__ void __launch_bounds__(128, 1) rows128_tc_kernel(int ny, int rows, const float* __restrict__ in, int ldi,
-                                                            const unsigned char* __restrict__ Spk,
-                                                            float* __restrict__ out, int ldo) {
+struct RowsSmem {
+  static constexpr int kStage = 2 * (kKC / 4) * 16 * 128;  // hi + lo of a 128-row chunk
+  static constexpr int S = 0;
+  static constexpr int raw = kRowChunks * kStage;
+  static constexpr int A = raw + kRawSlots * kRawBytes;
+  static constexpr int slab = A + kAStages * kStage;
+  static constexpr int bar = slab + 4 * 32 * kSlabStride * 4;
+  // rawfull[R], rawempty[R], afull[A], aempty[A], accf[2], acce[2], sbar
+  static constexpr int nbar = 2 * kRawSlots + 2 * kAStages + 5;
+  static constexpr int total = bar + nbar * 8 + 16;
+};
+static_assert(RowsSmem::total <= 232448, "row transform exceeds the shared memory of a CTA");
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* b, int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(kRowThreads, 1)
+    rows128_tc_kernel(const __grid_constant__ CUtensorMap tin, int ny, int rows,
+                      const unsigned char* __restrict__ Spk, float* __restrict__ out, int ldo) {
   using Md = TallMode<kTall3xTF32>;
   constexpr int T = Md::T;
-  constexpr int kBChunk = Md::NSPLIT * ((kKC / T) * (kRowN / 8) * 128);  // 16 KB
-  constexpr int kBAll = kRowChunks * kBChunk;                             // 128 KB
+  constexpr int kBChunk = RowsSmem::kStage;  // 16 KB of packed S per K chunk
   const int bB = Md::b_bytes(kRowN);
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* Bsm = smem;
-  unsigned char* Ast = smem + kBAll;                                      // [2][kAStage]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Ast + 2 * Md::kAStage);     // [0, 1] products, [2] S landed
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+  unsigned char* Ssm = smem + RowsSmem::S;
+  unsigned char* raw = smem + RowsSmem::raw;
+  unsigned char* Ast = smem + RowsSmem::A;
+  float* slab = reinterpret_cast<float*>(smem + RowsSmem::slab);
+  uint64_t* rawfull = reinterpret_cast<uint64_t*>(smem + RowsSmem::bar);
+  uint64_t* rawempty = rawfull + kRawSlots;
+  uint64_t* afull = rawempty + kRawSlots;
+  uint64_t* aempty = afull + kAStages;
+  uint64_t* accf = aempty + kAStages;
+  uint64_t* acce = accf + 2;
+  uint64_t* sbar = acce + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) {
+  if (warp == 9) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
-                 "r"(2 * kRowN));
+                 "r"(4 * kRowN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar + b)));
+    auto init = [](uint64_t* b, int n) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n));
+    };
+    for (int i = 0; i < kRawSlots; ++i) {
+      init(rawfull + i, 1);
+      init(rawempty + i, 4);
+    }
+    for (int i = 0; i < kAStages; ++i) {
+      init(afull + i, 4);
+      init(aempty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      init(accf + i, 1);
+      init(acce + i, 4);
+    }
+    init(sbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar + 2)), "r"(kBAll)
-                 : "memory");
-    for (int ch = 0; ch < kRowChunks; ++ch)
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              saddr(Bsm + ch * kBChunk)),
-          "l"(Spk + (size_t)ch * kBChunk), "r"(kBChunk), "r"(saddr(bar + 2))
-          : "memory");
-  }
-  const uint32_t idesc = instr_desc(2, 128, kRowN);
   const int tiles = (rows + 127) / 128;
-  bool ok = true, have_s = false;
-  int g = 0;  // chunks staged by this CTA so far
-  for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-    const int r = tile * 128 + tid;
-    const bool valid = r < rows;
-    const int c = valid ? r / ny : 0, j = valid ? r - c * ny : 0;
-    const float* rin = in + (size_t)c * ldi + (size_t)j * kRowN;
-    for (int ch = 0; ch < kRowChunks; ++ch, ++g) {
-      const int s = g & 1;
-      if (g >= 2) {
-        const bool w = mbar_wait(saddr(bar + s), ((g - 2) >> 1) & 1);
-        if (!__syncthreads_and(w)) {
+  bool ok = true;
+  if (warp == 8) {
+    // ---- loads: S once, then the raw K chunks of every tile
+    if (lane == 0) {
+      mbar_expect(sbar, kRowChunks * kBChunk);
+      for (int ch = 0; ch < kRowChunks; ++ch)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                saddr(Ssm + ch * kBChunk)),
+            "l"(Spk + (size_t)ch * kBChunk), "r"(kBChunk), "r"(saddr(sbar))
+            : "memory");
+      const uint64_t tmap = reinterpret_cast<uint64_t>(&tin);
+      int g = 0;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x)
+        for (int ch = 0; ch < kRowChunks; ++ch, ++g) {
+          const int i = g % kRawSlots;
+          if (g >= kRawSlots && !mbar_wait(saddr(rawempty + i), ((g / kRawSlots) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          mbar_expect(rawfull + i, kRawBytes);
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+              "[%4];" ::"r"(saddr(raw + i * kRawBytes)),
+              "l"(tmap), "r"(ch * kKC), "r"(tile * 128), "r"(saddr(rawfull + i))
+              : "memory");
+        }
+      // every copy issued has landed before the CTA exits
+      for (int u = (g > kRawSlots ? g - kRawSlots : 0); u < g; ++u)
+        mbar_wait(saddr(rawfull + u % kRawSlots), (u / kRawSlots) & 1);
+      mbar_wait(saddr(sbar), 0);
+      if (!ok) atomicExch(&g_tall_err, 1);
+    }
+  } else if (warp < 4) {
+    // ---- split: thread t converts K quarter t & 3 of rows t / 4 + 32 u
+    const int q = tid & 3;
+    int g = 0;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x)
+      for (int ch = 0; ch < kRowChunks; ++ch, ++g) {
+        const int i = g % kRawSlots, s = g % kAStages;
+        if (!__all_sync(0xffffffffu, mbar_wait(saddr(rawfull + i), (g / kRawSlots) & 1))) {
           ok = false;
           break;
         }
-      }
-      float v[kKC];
-      if (valid) {
+        float4 v[4];
 #pragma unroll
-        for (int q = 0; q < kKC / 4; ++q) {
-          const float4 x = *reinterpret_cast<const float4*>(rin + ch * kKC + 4 * q);
-          v[4 * q] = x.x;
-          v[4 * q + 1] = x.y;
-          v[4 * q + 2] = x.z;
-          v[4 * q + 3] = x.w;
+        for (int u = 0; u < 4; ++u)
+          v[u] = *reinterpret_cast<const float4*>(raw + i * kRawBytes + ((tid >> 2) + 32 * u) * (kKC * 4) + q * 16);
+        if (g >= kAStages && !__all_sync(0xffffffffu, mbar_wait(saddr(aempty + s), ((g / kAStages) - 1) & 1))) {
+          ok = false;
+          break;
         }
-      } else {
+        unsigned char* As = Ast + s * RowsSmem::kStage;
 #pragma unroll
-        for (int k = 0; k < kKC; ++k) v[k] = 0.f;
+        for (int u = 0; u < 4; ++u) {
+          const int r = (tid >> 2) + 32 * u;
+          put_row<kTall3xTF32>(As + (q * 16 + (r >> 3)) * 128 + (r & 7) * 16, Md::kABytes, &v[u].x);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        // the raw slot is released only after its values have been consumed, so
+        // no read of it is still in flight when the next copy overwrites it
+        if (lane == 0) {
+          mbar_arrive(afull + s);
+          mbar_arrive(rawempty + i);
+        }
       }
-      unsigned char* As = Ast + s * Md::kAStage;
-#pragma unroll
-      for (int q = 0; q < kKC / T; ++q)
-        put_row<kTall3xTF32>(As + (q * 16 + (tid >> 3)) * 128 + (tid & 7) * 16, Md::kABytes, v + q * T);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        if (!have_s) {
-          if (!mbar_wait(saddr(bar + 2), 0)) atomicExch(&g_tall_err, 1);
-          have_s = true;
+    if (!ok && lane == 0) atomicExch(&g_tall_err, 1);
+  } else if (warp == 9) {
+    // ---- products
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(2, 128, kRowN);
+      uint64_t* last = nullptr;
+      uint32_t lastpar = 0;
+      ok = mbar_wait(saddr(sbar), 0);
+      int g = 0, lt = 0;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++lt) {
+        const int b = lt & 1;
+        if (lt >= 2 && !mbar_wait(saddr(acce + b), ((lt >> 1) - 1) & 1)) {
+          ok = false;
+          break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = saddr(As), b0 = saddr(Bsm + ch * kBChunk);
-#pragma unroll
-        for (int ki = 0; ki < kKC / Md::KI; ++ki) {
-          const int q = ki * (Md::KI / T);
-#pragma unroll
-          for (int tm = 0; tm < 3; ++tm) {
-            // hi hi into columns 0..127; the two correction products hi lo and
-            // lo hi into columns 128..255, summed with the first in the epilogue
-            const int sa = (tm == 2) ? 1 : 0, sb = (tm == 1) ? 1 : 0;
-            const uint64_t ad = smem_desc(a0 + sa * Md::kABytes + q * 16 * 128, 16 * 128, 128);
-            const uint64_t bd = smem_desc(b0 + sb * bB + q * (kRowN / 8) * 128, (kRowN / 8) * 128, 128);
-            const uint32_t acc = (ch > 0 || ki > 0 || tm == 2) ? 1u : 0u;
-            const uint32_t dst = tmem + (tm > 0 ? (uint32_t)kRowN : 0u);
-            asm volatile(
-                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        for (int ch = 0; ch < kRowChunks; ++ch, ++g) {
+          const int s = g % kAStages;
+          if (!mbar_wait(saddr(afull + s), (g / kAStages) & 1)) {
+            ok = false;
+            break;
           }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         saddr(bar + s))
-                     : "memory");
-      }
-    }
-    if (!ok) break;
-    // the tile's products are done: read the accumulator row by row
-    const bool w = mbar_wait(saddr(bar + ((g - 1) & 1)), ((g - 1) >> 1) & 1);
-    if (!__syncthreads_and(w)) {
-      ok = false;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    float* rout = out + (size_t)c * ldo + (size_t)j * kRowN;
-    for (int cb = 0; cb < kRowN; cb += 8) {
-      uint32_t x[8], y[8];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
-                     "=r"(x[7])
-                   : "r"(ta));
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]),
-                     "=r"(y[7])
-                   : "r"(ta + (uint32_t)kRowN));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float o[8];
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = saddr(Ast + s * RowsSmem::kStage), b0 = saddr(Ssm + ch * kBChunk);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) o[i] = __uint_as_float(x[i]) + __uint_as_float(y[i]);
-      if (valid) {
-        *reinterpret_cast<float4*>(rout + cb) = make_float4(o[0], o[1], o[2], o[3]);
-        *reinterpret_cast<float4*>(rout + cb + 4) = make_float4(o[4], o[5], o[6], o[7]);
+          for (int ki = 0; ki < kKC / Md::KI; ++ki) {
+            const int qq = ki * (Md::KI / T);
+#pragma unroll
+            for (int tm = 0; tm < 3; ++tm) {
+              const int sa = (tm == 2) ? 1 : 0, sb = (tm == 1) ? 1 : 0;  // hi hi, hi lo, lo hi
+              const uint64_t ad = smem_desc(a0 + sa * Md::kABytes + qq * 16 * 128, 16 * 128, 128);
+              const uint64_t bd = smem_desc(b0 + sb * bB + qq * (kRowN / 8) * 128, (kRowN / 8) * 128, 128);
+              const uint32_t acc = (ch > 0 || ki > 0 || tm == 2) ? 1u : 0u;
+              const uint32_t dst = tmem + (uint32_t)(b * 2 * kRowN) + (tm > 0 ? (uint32_t)kRowN : 0u);
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           saddr(aempty + s))
+                       : "memory");
+          last = aempty + s;
+          lastpar = (g / kAStages) & 1;
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         saddr(accf + b))
+                     : "memory");
+        last = accf + b;
+        lastpar = (lt >> 1) & 1;
       }
+      if (last) mbar_wait(saddr(last), lastpar);  // the products issued have completed
+      if (!ok) atomicExch(&g_tall_err, 1);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // every warp has read the accumulator before the next tile overwrites it
+    __syncwarp();
+  } else {
+    // ---- epilogue: warp 4 + e writes rows 32 e .. 32 e + 31 of every tile
+    const int e = warp - 4;
+    float* sl = slab + e * 32 * kSlabStride;
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++lt) {
+      const int b = lt & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(saddr(accf + b), (lt >> 1) & 1))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int r = tile * 128 + e * 32 + lane;
+      const int c = r / ny, j = r - c * ny;
+      const long long base = r < rows ? (long long)c * ldo + (long long)j * kRowN : -1;
+#pragma unroll 1
+      for (int cb = 0; cb < kRowN; cb += 32) {
+        uint32_t x[32], y[32];
+        const uint32_t ta = tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(b * 2 * kRowN + cb);
+        // both halves and the wait in one statement: the registers are defined
+        // only once the wait has retired the loads (split statements let their
+        // consumers be scheduled ahead of the wait)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+            "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]),
+              "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]),
+              "=r"(x[15]), "=r"(x[16]), "=r"(x[17]), "=r"(x[18]), "=r"(x[19]), "=r"(x[20]), "=r"(x[21]),
+              "=r"(x[22]), "=r"(x[23]), "=r"(x[24]), "=r"(x[25]), "=r"(x[26]), "=r"(x[27]), "=r"(x[28]),
+              "=r"(x[29]), "=r"(x[30]), "=r"(x[31]),
+              "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]), "=r"(y[7]),
+              "=r"(y[8]), "=r"(y[9]), "=r"(y[10]), "=r"(y[11]), "=r"(y[12]), "=r"(y[13]), "=r"(y[14]),
+              "=r"(y[15]), "=r"(y[16]), "=r"(y[17]), "=r"(y[18]), "=r"(y[19]), "=r"(y[20]), "=r"(y[21]),
+              "=r"(y[22]), "=r"(y[23]), "=r"(y[24]), "=r"(y[25]), "=r"(y[26]), "=r"(y[27]), "=r"(y[28]),
+              "=r"(y[29]), "=r"(y[30]), "=r"(y[31])
+            : "r"(ta), "r"(ta + (uint32_t)kRowN)
+            : "memory");
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+          *reinterpret_cast<float4*>(sl + lane * kSlabStride + 4 * m) =
+              make_float4(__uint_as_float(x[4 * m]) + __uint_as_float(y[4 * m]),
+                          __uint_as_float(x[4 * m + 1]) + __uint_as_float(y[4 * m + 1]),
+                          __uint_as_float(x[4 * m + 2]) + __uint_as_float(y[4 * m + 2]),
+                          __uint_as_float(x[4 * m + 3]) + __uint_as_float(y[4 * m + 3]));
+        __syncwarp();
+        // eight lanes per 128-byte row segment, four rows per store instruction
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int rr = 4 * i + (lane >> 3), cc = (lane & 7) * 4;
+          const long long bi = __shfl_sync(0xffffffffu, base, rr);
+          const float4 v = *reinterpret_cast<const float4*>(sl + rr * kSlabStride + cc);
+          if (bi >= 0) *reinterpret_cast<float4*>(out + bi + cb + cc) = v;
+        }
+        __syncwarp();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce + b);
+    }
+    if (!ok && lane == 0) atomicExch(&g_tall_err, 1);
   }
-  if (!ok) {
-    if (tid == 0) atomicExch(&g_tall_err, 1);
-    if (g > 0) mbar_wait(saddr(bar + ((g - 1) & 1)), ((g - 1) >> 1) & 1);  // products already issued
-  }
-  if (tid == 0 && !have_s) mbar_wait(saddr(bar + 2), 0);  // the copy of S has landed
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kRowN));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 9) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * kRowN));
 }
 
 }  // namespace
@@ -513,13 +655,39 @@ int rows128_pack(const float* S, void* out, cudaStream_t st) {
   return SC4DVAR_OK;
 }
 
-int rows128_tc(int ny, int rows, const float* in, int ldi, const void* Spk, float* out, int ldo, cudaStream_t st) {
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+int rows128_tc(int ny, int rows, const float* in, const void* Spk, float* out, int ldo, cudaStream_t st) {
   if (rows <= 0) return SC4DVAR_OK;
-  const int smem = (int)rows128_pack_bytes() + 2 * TallMode<kTall3xTF32>::kAStage + 64;
-  SC4_CUDA(cudaFuncSetAttribute(rows128_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (ny <= 0 || ((uintptr_t)in % 16) != 0 || ((uintptr_t)out % 16) != 0 || ldo % 4 != 0 || !Spk)
+    return SC4DVAR_ERR_INVALID_ARG;
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc) return SC4DVAR_ERR_CUDA;
+  CUtensorMap tm;
+  const cuuint64_t dims[2] = {(cuuint64_t)kRowN, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kRowN * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kKC, 128u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(in), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return SC4DVAR_ERR_CUDA;
+  SC4_CUDA(cudaFuncSetAttribute(rows128_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, RowsSmem::total));
   const int tiles = div_up(rows, 128);
-  rows128_tc_kernel<<<std::min(tiles, 152), 128, smem, st>>>(ny, rows, in, ldi,
-                                                            static_cast<const unsigned char*>(Spk), out, ldo);
+  rows128_tc_kernel<<<std::min(tiles, 152), kRowThreads, RowsSmem::total, st>>>(
+      tm, ny, rows, static_cast<const unsigned char*>(Spk), out, ldo);
   SC4_LAUNCH_CHECK();
   return SC4DVAR_OK;
 }

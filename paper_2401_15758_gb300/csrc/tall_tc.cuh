@@ -13,13 +13,13 @@ template <typename TC>
 int tall_gemm_tc(int mode, int rows, int kk, int c, double alpha, const float* A, int lda, const double* B,
                  int ldb, int transB, double beta, TC* C, int ldc, void* pack, cudaStream_t st);
 // The 128-point row transform out[r][:] = in[r][:] S of the double-gyre
-// elliptic solves (rows r = c ny + j at in + c ldi + j 128, likewise out), S a
-// row-major 128 x 128 FP32 matrix packed once by rows128_pack into a device
-// buffer of rows128_pack_bytes(); 3xTF32 products on the tensor cores. in, out
-// 16-byte aligned, ldi and ldo multiples of 4.
+// elliptic solves (rows r = c ny + j of back-to-back fields: row r at in + 128 r,
+// its output at out + c ldo + 128 j), S a row-major 128 x 128 FP32 matrix packed
+// once by rows128_pack into a device buffer of rows128_pack_bytes(); 3xTF32
+// products on the tensor cores. in and out 16-byte aligned, ldo a multiple of 4.
 size_t rows128_pack_bytes();
 int rows128_pack(const float* S, void* out, cudaStream_t st);
-int rows128_tc(int ny, int rows, const float* in, int ldi, const void* Spk, float* out, int ldo, cudaStream_t st);
+int rows128_tc(int ny, int rows, const float* in, const void* Spk, float* out, int ldo, cudaStream_t st);
 // SC4DVAR_ERR_TIMEOUT (and clears it) if a tensor-core wait gave up since the last
 // call; synchronizes with the device.
 int tall_tc_take_error();
