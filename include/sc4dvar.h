@@ -339,6 +339,12 @@ int sc4dvar_build_precond(sc4dvar_problem_t p, const sc4dvar_sketch_opts* opts,
 int sc4dvar_precond_destroy(sc4dvar_precond_t P);
 /* rank l and, optionally, lam [l] (descending) and V (n x l, ld n) copied to host. */
 int sc4dvar_precond_info(sc4dvar_precond_t P, int* rank, double* lam_host, double* V_host);
+/* A preconditioner (I + V Lam V^T)^{-1} rebuilt from host copies of its factors
+ * (as sc4dvar_precond_info returns them): 0 <= l <= n, lam [l] finite and
+ * >= 0, V n x l (ld n), n the problem's size. It applies bit for bit like the
+ * original. ERR_INVALID_ARG for a bad l or lam. */
+int sc4dvar_precond_import(sc4dvar_problem_t p, int l, const double* lam_host, const double* V_host,
+                           sc4dvar_precond_t* out);
 /* Z = (I + V Lam V^T)^{-1} R (Eq. woodbury) for k columns, FP64. */
 int sc4dvar_precond_apply(sc4dvar_precond_t P, const double* R_dev, int ldr, int k,
                           double* Z_dev, int ldz, void* stream);
@@ -384,6 +390,41 @@ int sc4dvar_qr_update(int m, int r1, int r2, int k1, int k2, const double* P_dev
 int sc4dvar_gauss_newton(sc4dvar_problem_t p, const sc4dvar_gn_opts* opts, double* v_inout_dev,
                          sc4dvar_gn_info* info, void* stream);
 
+/* Gauss-Newton state at an iteration boundary, for checkpoint and resume (no
+ * counterpart in the paper). The sketch draws and the kappa_re probe of
+ * iteration k are keyed by k (Philox streams with gn_iter = k, and
+ * SC4DVAR_STREAM_KAPPA + k), so the iteration index is the whole random-number
+ * state. Together with the iterate v and the preconditioner held across the
+ * boundary it fixes every later iteration. */
+typedef struct {
+    int next_iter;         /* GN iterations completed = index of the next one     */
+    double g0_inf;         /* |g_0|_inf of the first iterate (the gtol reference) */
+    int sketch_iter;       /* iteration that built the held preconditioner (-1: none) */
+} sc4dvar_gn_state;
+
+/* Runs GN iterations state->next_iter .. opts->iters - 1 from v_inout with the
+ * steps of sc4dvar_gauss_newton, and leaves state at the boundary where it
+ * stopped: opts->iters, or the iteration at which gtol was met or an error
+ * occurred (v_inout then holds the iterate at that boundary).
+ *
+ * *held is the preconditioner carried over the boundary. On entry it is the
+ * one a previous call returned, one rebuilt by sc4dvar_precond_import, or NULL.
+ * The call takes ownership of it. On return *held is the preconditioner in use
+ * at the end (or NULL); whatever *held holds on return belongs to the caller,
+ * also after an error (sc4dvar_precond_destroy).
+ *
+ * state->next_iter == 0 starts a new run; info is then cleared. Otherwise the
+ * entries of info below next_iter are left as they are. info may be NULL;
+ * info->iters_done counts from iteration 0.
+ *
+ * A resumed run repeats an uninterrupted one bit for bit, except that its
+ * first iteration always runs a FWD and a gradient at v. (Across the boundary,
+ * a strong-Wolfe search would otherwise reuse its last trial's J and g.) The
+ * counters show that extra FWD and ADJ. Synchronizes. */
+int sc4dvar_gauss_newton_resume(sc4dvar_problem_t p, const sc4dvar_gn_opts* opts, double* v_inout_dev,
+                                sc4dvar_gn_state* state, sc4dvar_precond_t* held,
+                                sc4dvar_gn_info* info, void* stream);
+
 /* ---- batched serving ----------------------------------------------------------
  * A batch of independent problems (any mix of grids, windows, observations and
  * block widths). No counterpart in the paper: its experiments solve one problem
@@ -420,6 +461,8 @@ int sc4dvar_autotune(sc4dvar_problem_t p, int k, int* chosen);
 
 int sc4dvar_counters(sc4dvar_problem_t p, sc4dvar_counters_t* out);
 int sc4dvar_counters_reset(sc4dvar_problem_t p);
+/* Overwrites the problem's counters (to carry them across a GN checkpoint). */
+int sc4dvar_counters_set(sc4dvar_problem_t p, const sc4dvar_counters_t* c);
 
 /* Device Gaussian draw (the method's convention above): out (rows x cols, ld
  * rows, double) = columns col0.. of stream (seed, stream_id). */

@@ -93,6 +93,50 @@ class Precond:
             pass
 
 
+class GNCheckpoint:
+    """Gauss-Newton state at an iteration boundary, for checkpoint and resume.
+
+    v: the iterate (float64, (n,)). next_iter: the iterations completed, which is
+    also the random-number state (the sketch draws and the kappa_re probe of
+    iteration k are keyed by k). g0_inf: |g_0|_inf, the gtol reference. V, lam:
+    the factors (n, l) and (l,) of the preconditioner held across the boundary, or
+    None. sketch_iter: the iteration that built them (-1: none). counters: the
+    problem's counters. record: the per-iteration records of the iterations done.
+    save() and load() write and read one .npz file."""
+
+    FORMAT = 1
+
+    def __init__(self, v, next_iter, g0_inf, sketch_iter, V, lam, counters, record):
+        self.v = np.asarray(v, dtype=np.float64)
+        self.next_iter = int(next_iter)
+        self.g0_inf = float(g0_inf)
+        self.sketch_iter = int(sketch_iter)
+        self.V = None if V is None else np.asarray(V, dtype=np.float64)
+        self.lam = None if lam is None else np.asarray(lam, dtype=np.float64)
+        self.counters = {k: int(x) for k, x in dict(counters).items()}
+        self.record = [dict(r) for r in record]
+
+    def save(self, path):
+        import json
+        has = self.V is not None
+        np.savez(path, format=np.int64(self.FORMAT), v=self.v, next_iter=np.int64(self.next_iter),
+                 g0_inf=np.float64(self.g0_inf), sketch_iter=np.int64(self.sketch_iter),
+                 has_precond=np.int64(int(has)), V=self.V if has else np.zeros((self.v.shape[0], 0)),
+                 lam=self.lam if has else np.zeros(0),
+                 counters=np.array(json.dumps(self.counters)), record=np.array(json.dumps(self.record)))
+
+    @classmethod
+    def load(cls, path):
+        import json
+        with np.load(path, allow_pickle=False) as z:
+            if int(z["format"]) != cls.FORMAT:
+                raise ValueError(f"GN checkpoint format {int(z['format'])}, expected {cls.FORMAT}")
+            has = bool(int(z["has_precond"]))
+            return cls(z["v"], int(z["next_iter"]), float(z["g0_inf"]), int(z["sketch_iter"]),
+                       z["V"] if has else None, z["lam"] if has else None,
+                       json.loads(str(z["counters"])), json.loads(str(z["record"])))
+
+
 class Problem:
     """One SC-4DVAR assimilation window (handle of sc4dvar_problem_create).
 
@@ -290,22 +334,88 @@ class Problem:
         return x, {"iterations": info.iterations, "restarts": info.restarts,
                    "relres": info.relres, "status": info.status}
 
+    def _gn_opts(self, iters, method, l, adaptive, l2, l_hat, l_max, eps_sk, eps_re, tol, maxit, prec,
+                 refine, gtol, seed, line_search, ls_c1, ls_c2, ls_alpha1, solve, gemm):
+        so = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed, 0, prec,
+                             gemm)
+        return _abi.GnOpts(iters, gtol, so, eps_re, _abi.PcgOpts(tol, maxit, prec, refine),
+                           int(line_search), ls_c1, ls_c2, ls_alpha1, {"pcg": 0, "sketchsolv": 1}[solve])
+
+    @staticmethod
+    def _gn_records(info, lo, hi):
+        return [{"J": info.J[i], "g_inf": info.g_inf[i], "pcg_its": info.pcg_its[i],
+                 "relres": info.relres[i], "sketched": bool(info.sketched[i]),
+                 "rank": info.rank[i], "kappa_re": info.kappa_re[i], "alpha": info.alpha[i],
+                 "ls_evals": info.ls_evals[i], "ls_status": info.ls_status[i]} for i in range(lo, hi)]
+
     def gauss_newton(self, v, iters=3, method="none", l=20, adaptive=False, l2=0, l_hat=0,
                      l_max=0, eps_sk=1.01, eps_re=10.0, tol=1e-6, maxit=0, prec=FP64, refine=2,
                      gtol=0.0, seed=20240128, line_search=False, ls_c1=1e-4, ls_c2=0.9,
                      ls_alpha1=1.0, solve="pcg", stream=None, gemm=0):
         """Gauss-Newton in place on v (float64, (n,)); returns the per-iteration record."""
-        so = _abi.SketchOpts(METHODS[method], l, l2, int(adaptive), l_hat, l_max, eps_sk, seed, 0, prec,
-                             gemm)
-        o = _abi.GnOpts(iters, gtol, so, eps_re, _abi.PcgOpts(tol, maxit, prec, refine), int(line_search),
-                        ls_c1, ls_c2, ls_alpha1, {"pcg": 0, "sketchsolv": 1}[solve])
+        o = self._gn_opts(iters, method, l, adaptive, l2, l_hat, l_max, eps_sk, eps_re, tol, maxit, prec,
+                          refine, gtol, seed, line_search, ls_c1, ls_c2, ls_alpha1, solve, gemm)
         info = _abi.GnInfo()
         check(lib.sc4dvar_gauss_newton(self.h, C.byref(o), _ptr(v), C.byref(info), _stream(stream)))
-        k = info.iters_done
-        return [{"J": info.J[i], "g_inf": info.g_inf[i], "pcg_its": info.pcg_its[i],
-                 "relres": info.relres[i], "sketched": bool(info.sketched[i]),
-                 "rank": info.rank[i], "kappa_re": info.kappa_re[i], "alpha": info.alpha[i],
-                 "ls_evals": info.ls_evals[i], "ls_status": info.ls_status[i]} for i in range(k)]
+        return self._gn_records(info, 0, info.iters_done)
+
+    def gauss_newton_resume(self, v, iters, checkpoint=None, method="none", l=20, adaptive=False, l2=0,
+                            l_hat=0, l_max=0, eps_sk=1.01, eps_re=10.0, tol=1e-6, maxit=0, prec=FP64,
+                            refine=2, gtol=0.0, seed=20240128, line_search=False, ls_c1=1e-4, ls_c2=0.9,
+                            ls_alpha1=1.0, solve="pcg", stream=None, gemm=0):
+        """Gauss-Newton iterations up to `iters` (counted from the start of the run),
+        continuing from `checkpoint` (a GNCheckpoint; None starts a new run from v).
+        v (float64, (n,), on the device) receives the checkpoint's iterate first and
+        the final iterate on return. Returns (record of every iteration so far, the
+        GNCheckpoint at the boundary where this call stopped). The options must be
+        those of the interrupted run for the continuation to repeat it."""
+        o = self._gn_opts(iters, method, l, adaptive, l2, l_hat, l_max, eps_sk, eps_re, tol, maxit, prec,
+                          refine, gtol, seed, line_search, ls_c1, ls_c2, ls_alpha1, solve, gemm)
+        torch = _torch()
+        state = _abi.GnState(0, 0.0, -1)
+        held = C.c_void_p()
+        prev = []
+        if checkpoint is not None:
+            cp = checkpoint
+            if cp.v.shape != (self.n,):
+                raise ValueError(f"checkpoint of size {cp.v.shape}, problem of size {self.n}")
+            v.copy_(torch.as_tensor(cp.v, dtype=torch.float64, device=v.device))
+            state = _abi.GnState(cp.next_iter, cp.g0_inf, cp.sketch_iter)
+            self.counters_set(cp.counters)
+            if cp.V is not None:
+                held = C.c_void_p(self._precond_import_handle(cp.V, cp.lam))
+            prev = list(cp.record)[:cp.next_iter]
+        k0 = state.next_iter
+        info = _abi.GnInfo()
+        rc = lib.sc4dvar_gauss_newton_resume(self.h, C.byref(o), _ptr(v), C.byref(state), C.byref(held),
+                                             C.byref(info), _stream(stream))
+        # the preconditioner handed back is ours in every case: wrap it at once
+        held_pc = Precond(held.value, self.n) if held.value else None
+        check(rc)
+        record = prev + self._gn_records(info, k0, max(k0, info.iters_done))
+        V = lam = None
+        if held_pc is not None:
+            V, lam = held_pc.arrays()
+            held_pc.close()
+        cp_out = GNCheckpoint(v.detach().cpu().numpy().copy(), state.next_iter, state.g0_inf,
+                              state.sketch_iter if V is not None else -1, V, lam, self.counters(), record)
+        return record, cp_out
+
+    def _precond_import_handle(self, V, lam):
+        V = np.asarray(V, dtype=np.float64)
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+        if V.ndim != 2 or V.shape[0] != self.n or V.shape[1] != lam.shape[0]:
+            raise ValueError("V must be (n, l) and lam (l,)")
+        Vc = np.ascontiguousarray(V.T)  # column-major n x l
+        h = C.c_void_p()
+        check(lib.sc4dvar_precond_import(self.h, lam.shape[0], lam.ctypes.data_as(C.c_void_p),
+                                         Vc.ctypes.data_as(C.c_void_p), C.byref(h)))
+        return h.value
+
+    def precond_import(self, V, lam):
+        """A Precond rebuilt from host factors V (n, l) and lam (l,), e.g. those of
+        Precond.arrays() or of a GNCheckpoint."""
+        return Precond(self._precond_import_handle(V, lam), self.n)
 
     def counters(self):
         c = _abi.Counters()
@@ -314,6 +424,10 @@ class Problem:
 
     def counters_reset(self):
         check(lib.sc4dvar_counters_reset(self.h))
+
+    def counters_set(self, counters):
+        c = _abi.Counters(**{f: int(counters.get(f, 0)) for f, _ in _abi.Counters._fields_})
+        check(lib.sc4dvar_counters_set(self.h, C.byref(c)))
 
 
 class Batch:

@@ -89,6 +89,10 @@ class GnInfo(C.Structure):
     ]
 
 
+class GnState(C.Structure):
+    _fields_ = [("next_iter", C.c_int), ("g0_inf", C.c_double), ("sketch_iter", C.c_int)]
+
+
 class Counters(C.Structure):
     _fields_ = [("fwd", C.c_int64), ("tlm_online", C.c_int64), ("adj_online", C.c_int64),
                 ("tlm_offline", C.c_int64), ("adj_offline", C.c_int64),
@@ -128,8 +132,12 @@ SIGNATURES = {
     "sc4dvar_sketchsolv": (I, [P, P, P, P]),
     "sc4dvar_qr_update": (I, [I, I, I, I, I, P, I, P, I, P, I, P, I, P]),
     "sc4dvar_gauss_newton": (I, [P, C.POINTER(GnOpts), P, C.POINTER(GnInfo), P]),
+    "sc4dvar_gauss_newton_resume": (I, [P, C.POINTER(GnOpts), P, C.POINTER(GnState), C.POINTER(P),
+                                        C.POINTER(GnInfo), P]),
+    "sc4dvar_precond_import": (I, [P, I, P, P, C.POINTER(P)]),
     "sc4dvar_counters": (I, [P, C.POINTER(Counters)]),
     "sc4dvar_counters_reset": (I, [P]),
+    "sc4dvar_counters_set": (I, [P, C.POINTER(Counters)]),
     "sc4dvar_gaussian": (I, [U64, U64, I, I, C.c_int64, P, P]),
     "sc4dvar_batch_create": (I, [C.POINTER(P), I, C.POINTER(P)]),
     "sc4dvar_batch_destroy": (I, [P]),

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <type_traits>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -218,6 +219,7 @@ static int model_adj(Prob* P, const T* W, int ldw, int k, T* L, int ldl, cudaStr
 // ------------------------------------------------------------------ operators
 template <typename T>
 static int tlm_block(Prob* P, const T* X, int ldx, int k, T* W, int ldw, cudaStream_t st) {
+  NvtxRange r("sc4dvar TLM block sweep");
   SC4_TRY(P->wU.ensure((size_t)P->n * k * sizeof(T)));
   T* U = P->wU.as<T>();
   SC4_TRY(prior_any<T, T, T>(P, k, X, ldx, U, P->n, (const T*)nullptr, 0, st));
@@ -229,6 +231,7 @@ static int tlm_block(Prob* P, const T* X, int ldx, int k, T* W, int ldw, cudaStr
 template <typename T>
 static int adj_block(Prob* P, const T* W, int ldw, int k, T* X, int ldx, const T* addZ, int ldz,
                      cudaStream_t st) {
+  NvtxRange r("sc4dvar ADJ block sweep");
   SC4_TRY(P->wL.ensure((size_t)P->n * k * sizeof(T)));
   T* L = P->wL.as<T>();
   SC4_TRY(model_adj<T>(P, W, ldw, k, L, P->n, st));
@@ -1033,6 +1036,7 @@ static int pcg_run(Prob* P, Prec* pc, const double* b, double* x, const sc4dvar_
     while (it < maxit && total_its < maxit * (max_restarts + 1)) {
       ++it;
       ++total_its;
+      NvtxRange r_it("sc4dvar PCG iteration");
       SC4_TRY(hvp_vec(P, p, q, o.prec, st));
       double pq;
       SC4_TRY(vdot<double, double>(n, p, q, sc, part, st));
@@ -1087,6 +1091,7 @@ static int pcg_run(Prob* P, Prec* pc, const double* b, double* x, const sc4dvar_
 
 // ------------------------------------------------------------------ model runs
 static int fwd_run(Prob* P, const double* v, double* J_host, double* d_out, cudaStream_t st) {
+  NvtxRange r("sc4dvar FWD");
   const int n = P->n, m = P->m;
   if (v != P->v) SC4_CUDA(cudaMemcpyAsync(P->v, v, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   SC4_TRY(prior_any<double, double, double>(P, 1, P->v, n, P->x0, n, P->xb, n, st));
@@ -1117,6 +1122,7 @@ static int fwd_run(Prob* P, const double* v, double* J_host, double* d_out, cuda
 }
 
 static int gradient_run(Prob* P, double* g, cudaStream_t st) {
+  NvtxRange r("sc4dvar gradient (ADJ)");
   if (!P->have_traj) {
     set_error("gradient: no forward trajectory (call sc4dvar_fwd first)");
     return SC4DVAR_ERR_STATE;
@@ -1132,6 +1138,7 @@ static int gradient_run(Prob* P, double* g, cudaStream_t st) {
 
 static int build_precond_impl(Prob* P, const sc4dvar_sketch_opts& o, const double* Om,
                               const double* Ps, Prec** out, cudaStream_t st) {
+  NvtxRange r("sc4dvar sketch");
   if (!P->have_traj) {
     set_error("build_precond: no forward trajectory (call sc4dvar_fwd first)");
     return SC4DVAR_ERR_STATE;
@@ -1790,28 +1797,39 @@ static int line_search(Prob* P, const double* v, const double* dv, double* vt, d
   return finish(a_prev, f_prev, kLsMaxEvals, false);
 }
 
-int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* v_io,
-                         sc4dvar_gn_info* info, void* stream) {
-  SC4_ARG(P && o && v_io, "null argument");
+int sc4dvar_gauss_newton_resume(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* v_io,
+                                sc4dvar_gn_state* state, sc4dvar_precond_t* held, sc4dvar_gn_info* info,
+                                void* stream) {
+  SC4_ARG(P && o && v_io && state && held, "null argument");
   SC4_ARG(o->iters >= 1 && o->iters <= SC4DVAR_GN_MAX_ITERS, "iters");
+  SC4_ARG(state->next_iter >= 0 && state->next_iter <= o->iters, "state->next_iter in [0, iters]");
+  SC4_ARG(state->next_iter > 0 || *held == nullptr, "a new run (next_iter = 0) holds no preconditioner");
+  SC4_ARG(*held == nullptr || (*held)->n == P->n, "held preconditioner of another size");
   SC4_ARG(!o->line_search || (o->ls_c1 > 0 && o->ls_c1 < o->ls_c2 && o->ls_c2 < 1 && o->ls_alpha1 > 0),
           "line search constants: 0 < c1 < c2 < 1, alpha1 > 0");
   SC4_ARG(o->solve == 0 || (o->solve == 1 && o->sketch.method != SC4DVAR_SKETCH_NONE),
           "solve: 0 (PCG) or 1 (SketchSolv, needs a sketch method)");
   cudaStream_t st = S(stream);
   const int n = P->n;
-  if (info) std::memset(info, 0, sizeof(*info));
+  const int k0 = state->next_iter;
+  if (info && k0 == 0) std::memset(info, 0, sizeof(*info));
   Buf gb;
   SC4_TRY(gb.ensure((size_t)3 * n * sizeof(double)));
   double* g = gb.as<double>();
   double* dv = g + n;
   double* vt = dv + n;
-  Prec* pc = nullptr;
-  double g0 = 0;
+  Prec* pc = *held;
+  *held = nullptr;
+  double g0 = k0 > 0 ? state->g0_inf : 0.0;
+  int sketch_iter = pc ? state->sketch_iter : -1;
   int rc = SC4DVAR_OK;
   bool carry = false;  // J and g at v_io come from the last line-search trial
   double J = 0.0;
-  for (int k = 0; k < o->iters; ++k) {
+  int k = k0;
+  char label[48];
+  for (; k < o->iters; ++k) {
+    std::snprintf(label, sizeof(label), "sc4dvar GN iteration %d", k);
+    NvtxRange r_it(label);
     if (!carry) {
       if ((rc = fwd_run(P, v_io, &J, nullptr, st))) break;
       if ((rc = gradient_run(P, g, st))) break;
@@ -1828,6 +1846,7 @@ int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* 
     }
     if (k > 0 && o->gtol > 0 && ginf / g0 < o->gtol) break;
     if (o->sketch.method != SC4DVAR_SKETCH_NONE) {
+      NvtxRange r_sk("sc4dvar sketch or reuse");
       bool need = (pc == nullptr) || !o->sketch.adaptive;
       if (!need) {
         double kre;
@@ -1840,9 +1859,11 @@ int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* 
       if (need) {
         precond_free(pc);
         pc = nullptr;
+        sketch_iter = -1;
         sc4dvar_sketch_opts so = o->sketch;
         so.gn_iter = k;
         if ((rc = build_precond_impl(P, so, nullptr, nullptr, &pc, st))) break;
+        sketch_iter = k;
         if (info) info->sketched[k] = 1;
       }
       if (info) info->rank[k] = pc->l;
@@ -1863,6 +1884,7 @@ int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* 
     }
     double alpha = 1.0;
     if (o->line_search) {
+      NvtxRange r_ls("sc4dvar line search");
       // phi'(0) = g^T dv with g = -b
       double gdv;
       if ((rc = vdot<double, double>(n, g, dv, P->scal.as<double>(), P->part.as<double>(), st))) break;
@@ -1883,9 +1905,52 @@ int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* 
     if ((rc = axpby<double, double>(n, alpha, dv, 1.0, v_io, st))) break;
   }
   cudaStreamSynchronize(st);
-  precond_free(pc);
   gb.release();
+  state->next_iter = k;
+  state->g0_inf = g0;
+  state->sketch_iter = pc ? sketch_iter : -1;
+  *held = pc;
   return rc;
+}
+
+int sc4dvar_gauss_newton(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, double* v_io,
+                         sc4dvar_gn_info* info, void* stream) {
+  sc4dvar_gn_state state{0, 0.0, -1};
+  sc4dvar_precond_t held = nullptr;
+  const int rc = sc4dvar_gauss_newton_resume(P, o, v_io, &state, &held, info, stream);
+  precond_free(held);
+  return rc;
+}
+
+int sc4dvar_precond_import(sc4dvar_problem_t P, int l, const double* lam_host, const double* V_host,
+                           sc4dvar_precond_t* out) {
+  SC4_ARG(P && out, "null argument");
+  SC4_ARG(l >= 0 && l <= P->n, "precond_import: 0 <= l <= n");
+  SC4_ARG(l == 0 || (lam_host && V_host), "precond_import: lam and V needed for l > 0");
+  std::vector<double> lam_dsc(2 * (size_t)l);
+  for (int i = 0; i < l; ++i) {
+    const double lm = lam_host[i];
+    SC4_ARG(std::isfinite(lm) && lm >= 0.0, "precond_import: lam finite and >= 0");
+    lam_dsc[i] = lm;
+    lam_dsc[l + i] = lm / (1.0 + lm);  // as the sketches form it on the device (IEEE division)
+  }
+  Prec* pc = new Prec();
+  pc->n = P->n;
+  pc->l = l;
+  if (l > 0) {
+    if (cudaMalloc(&pc->V, (size_t)P->n * l * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&pc->lam, 2 * (size_t)l * sizeof(double)) != cudaSuccess ||
+        cudaMemcpy(pc->V, V_host, (size_t)P->n * l * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pc->lam, lam_dsc.data(), 2 * (size_t)l * sizeof(double), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      precond_free(pc);
+      sc4::set_error("precond_import: device allocation or copy failed");
+      return SC4DVAR_ERR_CUDA;
+    }
+    pc->dsc = pc->lam + l;
+  }
+  *out = pc;
+  return SC4DVAR_OK;
 }
 
 int sc4dvar_counters(sc4dvar_problem_t P, sc4dvar_counters_t* out) {
@@ -1897,6 +1962,12 @@ int sc4dvar_counters(sc4dvar_problem_t P, sc4dvar_counters_t* out) {
 int sc4dvar_counters_reset(sc4dvar_problem_t P) {
   SC4_ARG(P, "null argument");
   P->counters = sc4dvar_counters_t{};
+  return SC4DVAR_OK;
+}
+
+int sc4dvar_counters_set(sc4dvar_problem_t P, const sc4dvar_counters_t* c) {
+  SC4_ARG(P && c, "null argument");
+  P->counters = *c;
   return SC4DVAR_OK;
 }
 

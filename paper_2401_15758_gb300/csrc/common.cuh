@@ -1,11 +1,22 @@
 // Shared device/host helpers of the sc4dvar CUDA library.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string>
 #include "../../include/sc4dvar.h"
 
 namespace sc4 {
+
+// ---- tracing ------------------------------------------------------------------
+// An NVTX range for the lifetime of the object (GN iterations, sketches, sweeps,
+// PCG iterations); a no-op unless a profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- error plumbing ---------------------------------------------------------
 void set_error(const std::string& msg);
