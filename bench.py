@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--gn-iters", type=int, default=25,
                     help="GN iterations of the double-gyre experiment (the paper runs 25) and of the "
                          "1024^2 vorticity comparison (its workload: 5)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the double-gyre and 64-problem batch measurements of the default run")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: first 40 output steps, one TLM and one ADJ block")
     ap.add_argument("--profile-sketch", action="store_true",
@@ -427,9 +429,10 @@ def bve_arm(args):
     print(json.dumps(out), flush=True)
 
 
-def batch_arm(args):
+def batch_arm(args, emit=True):
     """64 uneven Burgers problems: one graph-replayed batched block Hessian
-    product (FP32 sweeps) per step; HVP/s = sum of the block widths / time."""
+    product (FP32 sweeps) per step; HVP/s = sum of the block widths / time.
+    Prints its JSON line, or returns it with emit=False."""
     import torch
     import paper_2401_15758_gb300 as g
     import sc4dvar_inputs as si
@@ -499,6 +502,11 @@ def batch_arm(args):
            "batched_pcg": {"ms_per_iteration": pcg_ms, "problems": len(probs),
                            "note": "one graph launch = one FP32-operator PCG iteration of all 64 problems",
                            "iterations_done": int(max(its)), "max_relres": float(max(rel))}}
+    b.close()
+    for p in probs:
+        p.close()
+    if not emit:
+        return out
     print(json.dumps(out), flush=True)
 
 
@@ -599,7 +607,7 @@ def paper_arm(args):
     print(json.dumps(out), flush=True)
 
 
-def gyre_arm(args):
+def gyre_arm(args, emit=True):
     """The barotropic vorticity experiment of Sec. 5.2 (double gyre in a closed
     basin, 128 x 257 interior points, RK3-TVD, 40 steps, 8 observation times of
     a 16 x 16 sensor grid): 25 GN iterations, PCG to 1e-9, strong-Wolfe steps,
@@ -703,6 +711,8 @@ def gyre_arm(args):
            "single_fp64_product_ms": 1e3 * t1,
            "gpu_launches_per_step": int(launches), "clocks": clk,
            "gn_step": gn, "paper_table4_comparison": rows}
+    if not emit:
+        return out
     print(json.dumps(out), flush=True)
 
 
@@ -856,6 +866,18 @@ def gpu_arm(args):
     if not args.no_bve and world == 1:
         prob.close()
         bve = bve_block("bve_n256", steps=3, warmup=3, with_gn=not args.no_gn_step)
+    # the double-gyre experiment's block products (Sec. 5.2, FP64 and FP32, k =
+    # 384) and the 64-problem batch, as further measurements on the same GPU
+    extras = {}
+    if not args.no_extras and world == 1:
+        prob.close()
+        ns = argparse.Namespace(steps=3, warmup=3, gn_iters=0, no_gn_step=True)
+        gy = gyre_arm(ns, emit=False)
+        extras["bve_gyre"] = {k: gy[k] for k in ("value", "unit", "ms_per_step", "dtype", "roofline", "config",
+                                                 "fp32_block", "gpu_launches_per_step", "clocks")}
+        bt = batch_arm(ns, emit=False)
+        extras["burgers_batch64"] = {k: bt[k] for k in ("value", "unit", "ms_per_step", "dtype", "roofline",
+                                                        "config", "gpu_launches", "batched_pcg", "clocks")}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "HVP/s", "n_gpus": world,
@@ -868,6 +890,7 @@ def gpu_arm(args):
             out["gn_step"] = gn
         if bve is not None:
             out["bve_n256"] = bve
+        out.update(extras)
         if not args.no_cpu_baseline:
             dt, v, cores, desc = oracle_sample_parallel()
             dt1, v1, desc1 = oracle_sample()

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include "common.cuh"
+#include "cluster.cuh"
 #include "model.cuh"
 
 namespace cg = cooperative_groups;
@@ -217,13 +218,7 @@ __global__ void __launch_bounds__(Bounds2<P>::kThreads, 1) tlm_f32x2_kernel(
   f2* stage = sm + 2 * Hs;             // Hs + 2 kPad2
   f2* slots = stage + Hs + 2 * kPad2;  // [parity 2][array 2][L/R 2][32]
   int crank, csize;
-  if constexpr (CL) {
-    crank = (int)cg::this_cluster().block_rank();
-    csize = (int)cg::this_cluster().num_blocks();
-  } else {
-    crank = 0;
-    csize = 1;
-  }
+  cluster_pos<CL>(crank, csize);
   const EdgeNb2 enb = edge_nb2<CL>(slots, w, nw, crank, csize);
   const int col = blockIdx.x / csize;
   const int i0 = crank * Hs + tid * P;  // first pair of mine
@@ -298,6 +293,7 @@ __global__ void __launch_bounds__(Bounds2<P>::kThreads, 1) tlm_f32x2_kernel(
 #pragma unroll
     for (int p = 0; p < P; ++p) dx[p] = fma2(h2, acc[p], dx[p]);
   }
+  cluster_leave<CL>();  // no CTA leaves while a peer may still reach its shared memory
 }
 
 // ---------------------------------------------------------------- ADJ
@@ -314,13 +310,7 @@ __global__ void __launch_bounds__(Bounds2<P>::kThreads, 1) adj_f32x2_kernel(
   f2* buf[4] = {sm, sm + S, sm + 2 * S, sm + 3 * S};
   f2* slots = sm + 4 * S;  // [parity 2][L/R 2][32]
   int crank, csize;
-  if constexpr (CL) {
-    crank = (int)cg::this_cluster().block_rank();
-    csize = (int)cg::this_cluster().num_blocks();
-  } else {
-    crank = 0;
-    csize = 1;
-  }
+  cluster_pos<CL>(crank, csize);
   const EdgeNb2 enb = edge_nb2<CL>(slots, w, nw, crank, csize);
   const RowNb2<P> rnb(tid, NT, Hs, crank, csize);
   const int col = blockIdx.x / csize;
@@ -442,6 +432,7 @@ __global__ void __launch_bounds__(Bounds2<P>::kThreads, 1) adj_f32x2_kernel(
     out[i0 + p] = lam[p].x;
     out[g.H + i0 + p] = lam[p].y;
   }
+  cluster_leave<CL>();  // no CTA leaves while a peer may still reach its shared memory
 }
 
 // ---------------------------------------------------------------- one-CTA sweeps, factored stencils

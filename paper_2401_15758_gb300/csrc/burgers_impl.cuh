@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include "common.cuh"
+#include "cluster.cuh"
 #include "model.cuh"
 
 namespace cg = cooperative_groups;
@@ -80,17 +81,6 @@ __device__ __forceinline__ void put(T* arr, int jl, int seg, T v, int crank, int
   }
 }
 
-template <bool CL>
-__device__ __forceinline__ void cluster_pos(int& crank, int& csize) {
-  if constexpr (CL) {
-    auto c = cg::this_cluster();
-    crank = (int)c.block_rank();
-    csize = (int)c.num_blocks();
-  } else {
-    crank = 0;
-    csize = 1;
-  }
-}
 
 // f(U) at local index i (halo-padded array)
 template <typename T>
@@ -164,6 +154,7 @@ __global__ void __launch_bounds__(1024) burgers_fwd_kernel(
 #pragma unroll
     for (int p = 0; p < P; ++p) xN[j0 + threadIdx.x + p * NT] = x[p];
   }
+  cluster_leave<CL>();  // no CTA leaves while a peer may still reach its shared memory
 }
 
 // ---------------------------------------------------------------- TLM
@@ -233,6 +224,7 @@ __global__ void __launch_bounds__(1024) burgers_tlm_kernel(
 #pragma unroll
     for (int p = 0; p < P; ++p) dx[p] += pr.h * acc[p];
   }
+  cluster_leave<CL>();  // no CTA leaves while a peer may still reach its shared memory
 }
 
 // ---------------------------------------------------------------- ADJ
@@ -320,6 +312,7 @@ __global__ void __launch_bounds__(1024) burgers_adj_kernel(
   T* out = Out + (size_t)col * ldo;
 #pragma unroll
   for (int p = 0; p < P; ++p) out[j0 + threadIdx.x + p * NT] = lam[p];
+  cluster_leave<CL>();  // no CTA leaves while a peer may still reach its shared memory
 }
 
 }  // namespace sc4

@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(Bounds<T, P>::kThreads, 1) burgers_tlm_v2_kern
 #pragma unroll
     for (int p = 0; p < P; ++p) dx[p] += h * acc[p];
   }
+  cluster_leave<CL>();  // no CTA leaves while a peer may still reach its shared memory
 }
 
 // ---------------------------------------------------------------- ADJ (v2)
@@ -443,6 +444,7 @@ __global__ void __launch_bounds__(Bounds<T, P>::kThreads, 1) burgers_adj_v2_kern
     for (int p = 0; p < P; ++p) lam[p] += th[p];
   }
   store_row<T, P>(Out + (size_t)col * ldo + my0, lam);
+  cluster_leave<CL>();  // no CTA leaves while a peer may still reach its shared memory
 }
 
 // ---------------------------------------------------------------- FWD (v2)
@@ -516,6 +518,7 @@ __global__ void __launch_bounds__(Bounds<T, P>::kThreads, 1) burgers_fwd_v2_kern
     for (int p = 0; p < P; ++p) x[p] += h * acc[p];
   }
   if (xN) store_row<T, P>(xN + my0, x);
+  cluster_leave<CL>();  // no CTA leaves while a peer may still reach its shared memory
 }
 
 }  // namespace sc4
