@@ -332,18 +332,19 @@ int launch_tall(int rows, int kk, int c, double alpha, const float* A, int lda, 
 // persistent CTA keeps the packed S in shared memory and walks 128-row tiles
 // with four roles that run ahead of one another through mbarrier rings (every
 // wait bounded, its verdict made uniform across the warp):
-//   warp 8 (one thread)  tensor-memory-access loads of the raw FP32 K chunks of
-//                        the rows (2D tensor map, box 16 x 128) into a ring of
-//                        kRawSlots slots;
-//   warps 0-3            split each chunk into TF32 hi and lo parts in the
+//   loader warp (one thread)  tensor-memory-access loads of the raw FP32 K
+//                        chunks of the rows (2D tensor map, box 16 x 128) into a
+//                        ring of kRawSlots slots;
+//   splitting warps      two groups of four warps that take the chunks in turn
+//                        and split each into TF32 hi and lo parts in the
 //                        canonical K-major operand layout (kAStages stages);
-//   warp 9 (one thread)  six tcgen05 MMAs per chunk: hi hi into accumulator
+//   MMA warp (one thread) six tcgen05 MMAs per chunk: hi hi into accumulator
 //                        columns 0..127, hi lo and lo hi into 128..255 (summed
 //                        in the epilogue), two such accumulators (all 512 TMEM
 //                        columns) so that one tile's products overlap the
 //                        previous tile's epilogue;
-//   warps 4-7            read an accumulator with tcgen05.ld (warp 4 + w owns
-//                        TMEM lanes 32w .. 32w + 31), add its two halves and
+//   epilogue warps       read an accumulator with tcgen05.ld (epilogue warp w
+//                        owns TMEM lanes 32w .. 32w + 31), add its two halves and
 //                        write the rows through a per-warp shared slab of 32
 //                        columns, so that every store instruction covers four
 //                        128-byte row segments.
@@ -352,7 +353,13 @@ constexpr int kRowChunks = kRowN / kKC;
 constexpr int kRawSlots = 4;
 constexpr int kAStages = 3;
 constexpr int kRawBytes = kKC * kRowN * 4;  // 16 floats of 128 rows
-constexpr int kRowThreads = 320;
+// warps: kConvW splitting warps, 4 epilogue warps, one loader and one MMA warp
+template <int CW>
+struct RowsRoles {
+  static_assert(CW % 4 == 0, "the epilogue warps must start at a multiple of four (TMEM lane quarters)");
+  static constexpr int kEpi0 = CW, kLoad = CW + 4, kMma = CW + 5, kThreads = (CW + 6) * 32;
+};
+constexpr int kConvW = 8;  // two groups: 41.6 -> 36.4 us per k = 384 transform against one group
 constexpr int kSlabStride = 36;             // floats per slab row (16-byte rows, no bank conflicts)
 
 struct RowsSmem {
@@ -376,10 +383,12 @@ __device__ __forceinline__ void mbar_expect(uint64_t* b, int bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
 }
 
-__global__ void __launch_bounds__(kRowThreads, 1)
+template <int CW>
+__global__ void __launch_bounds__(RowsRoles<CW>::kThreads, 1)
     rows128_tc_kernel(const __grid_constant__ CUtensorMap tin, int ny, int rows,
                       const unsigned char* __restrict__ Spk, float* __restrict__ out, int ldo) {
   using Md = TallMode<kTall3xTF32>;
+  using Ro = RowsRoles<CW>;
   constexpr int T = Md::T;
   constexpr int kBChunk = RowsSmem::kStage;  // 16 KB of packed S per K chunk
   const int bB = Md::b_bytes(kRowN);
@@ -397,7 +406,7 @@ __global__ void __launch_bounds__(kRowThreads, 1)
   uint64_t* sbar = acce + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 9) {
+  if (warp == Ro::kMma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
                  "r"(4 * kRowN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -427,7 +436,7 @@ __global__ void __launch_bounds__(kRowThreads, 1)
   const uint32_t tmem = *tslot;
   const int tiles = (rows + 127) / 128;
   bool ok = true;
-  if (warp == 8) {
+  if (warp == Ro::kLoad) {
     // ---- loads: S once, then the raw K chunks of every tile
     if (lane == 0) {
       mbar_expect(sbar, kRowChunks * kBChunk);
@@ -459,12 +468,16 @@ __global__ void __launch_bounds__(kRowThreads, 1)
       mbar_wait(saddr(sbar), 0);
       if (!ok) atomicExch(&g_tall_err, 1);
     }
-  } else if (warp < 4) {
-    // ---- split: thread t converts K quarter t & 3 of rows t / 4 + 32 u
-    const int q = tid & 3;
+  } else if (warp < CW) {
+    // ---- split: CW / 4 groups of four warps take the K chunks in turn (two
+    // chunks in flight with eight warps); in a group, thread t converts K
+    // quarter t & 3 of rows t / 4 + 32 u
+    constexpr int kGroups = CW / 4;
+    const int grp = warp >> 2, gt = tid & 127, q = gt & 3;
     int g = 0;
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x)
       for (int ch = 0; ch < kRowChunks; ++ch, ++g) {
+        if (g % kGroups != grp) continue;
         const int i = g % kRawSlots, s = g % kAStages;
         if (!__all_sync(0xffffffffu, mbar_wait(saddr(rawfull + i), (g / kRawSlots) & 1))) {
           ok = false;
@@ -473,7 +486,7 @@ __global__ void __launch_bounds__(kRowThreads, 1)
         float4 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          v[u] = *reinterpret_cast<const float4*>(raw + i * kRawBytes + ((tid >> 2) + 32 * u) * (kKC * 4) + q * 16);
+          v[u] = *reinterpret_cast<const float4*>(raw + i * kRawBytes + ((gt >> 2) + 32 * u) * (kKC * 4) + q * 16);
         if (g >= kAStages && !__all_sync(0xffffffffu, mbar_wait(saddr(aempty + s), ((g / kAStages) - 1) & 1))) {
           ok = false;
           break;
@@ -481,7 +494,7 @@ __global__ void __launch_bounds__(kRowThreads, 1)
         unsigned char* As = Ast + s * RowsSmem::kStage;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int r = (tid >> 2) + 32 * u;
+          const int r = (gt >> 2) + 32 * u;
           put_row<kTall3xTF32>(As + (q * 16 + (r >> 3)) * 128 + (r & 7) * 16, Md::kABytes, &v[u].x);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -494,7 +507,7 @@ __global__ void __launch_bounds__(kRowThreads, 1)
         }
       }
     if (!ok && lane == 0) atomicExch(&g_tall_err, 1);
-  } else if (warp == 9) {
+  } else if (warp == Ro::kMma) {
     // ---- products
     if (lane == 0) {
       const uint32_t idesc = instr_desc(2, 128, kRowN);
@@ -551,8 +564,8 @@ __global__ void __launch_bounds__(kRowThreads, 1)
     }
     __syncwarp();
   } else {
-    // ---- epilogue: warp 4 + e writes rows 32 e .. 32 e + 31 of every tile
-    const int e = warp - 4;
+    // ---- epilogue: warp kEpi0 + e writes rows 32 e .. 32 e + 31 of every tile
+    const int e = warp - Ro::kEpi0;
     float* sl = slab + e * 32 * kSlabStride;
     int lt = 0;
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++lt) {
@@ -617,7 +630,7 @@ __global__ void __launch_bounds__(kRowThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (warp == 9) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * kRowN));
+  if (warp == Ro::kMma) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * kRowN));
 }
 
 }  // namespace
@@ -684,9 +697,10 @@ int rows128_tc(int ny, int rows, const float* in, const void* Spk, float* out, i
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return SC4DVAR_ERR_CUDA;
-  SC4_CUDA(cudaFuncSetAttribute(rows128_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, RowsSmem::total));
+  auto kern = rows128_tc_kernel<kConvW>;
+  SC4_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, RowsSmem::total));
   const int tiles = div_up(rows, 128);
-  rows128_tc_kernel<<<std::min(tiles, 152), kRowThreads, RowsSmem::total, st>>>(
+  kern<<<std::min(tiles, 152), RowsRoles<kConvW>::kThreads, RowsSmem::total, st>>>(
       tm, ny, rows, static_cast<const unsigned char*>(Spk), out, ldo);
   SC4_LAUNCH_CHECK();
   return SC4DVAR_OK;

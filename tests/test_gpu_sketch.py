@@ -344,3 +344,25 @@ def test_fp32_sketch_with_other_tall_product_arithmetic(small, gemm, tol):
     b = torch.tensor(np.random.default_rng(2).standard_normal(wl.n), device="cuda")
     x, info = prob.pcg(b, pc, tol=1e-8)
     assert info["status"] == 0 and info["iterations"] <= 12
+
+
+@pytest.mark.parametrize("method", ["randsvd", "nystrom", "singleview"])
+def test_sketchsolv_step_within_the_thm4_bound(small, method):
+    """Thm. 4 on the GPU's SketchSolv step: |dv - dv_hat| / |dv| <= |H - H_hat|_2
+    (the Gamma^{-1} norm of the paper is the 2-norm in v). H is the dense misfit
+    Hessian from the FP64 block product of the identity, dv the dense solve of
+    (I + H) dv = -g, H_hat = V diag(lam) V^T from the GPU sketch."""
+    wl, prob, _ = small
+    n = wl.n
+    H = prob.gn_hessian_apply_block(torch.eye(n, dtype=torch.float64, device="cuda"),
+                                    misfit_only=True).cpu().numpy()
+    H = 0.5 * (H + H.T)
+    P = prob.build_precond(method, l=12, l2=25)
+    V, lam = P.arrays()
+    normE = np.linalg.norm(H - (V * lam) @ V.T, 2)
+    g = np.random.default_rng(11).standard_normal(n)
+    dvh = P.sketchsolv(torch.tensor(g, device="cuda")).cpu().numpy()
+    dv = -np.linalg.solve(np.eye(n) + H, g)
+    err = np.linalg.norm(dv - dvh) / np.linalg.norm(dv)
+    assert 0.0 < normE
+    assert err <= normE * (1 + 1e-9) + 1e-12
