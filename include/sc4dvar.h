@@ -414,8 +414,10 @@ typedef struct {
  * also after an error (sc4dvar_precond_destroy).
  *
  * state->next_iter == 0 starts a new run; info is then cleared. Otherwise the
- * entries of info below next_iter are left as they are. info may be NULL;
- * info->iters_done counts from iteration 0.
+ * entries of info below next_iter are left as they are and those from
+ * next_iter on are cleared first. info may be NULL; info->iters_done counts
+ * from iteration 0. A held preconditioner needs a sketch method in opts
+ * (ERR_INVALID_ARG with SC4DVAR_SKETCH_NONE).
  *
  * A resumed run repeats an uninterrupted one bit for bit, except that its
  * first iteration always runs a FWD and a gradient at v. (Across the boundary,

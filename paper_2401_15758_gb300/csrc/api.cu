@@ -1805,6 +1805,8 @@ int sc4dvar_gauss_newton_resume(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, d
   SC4_ARG(state->next_iter >= 0 && state->next_iter <= o->iters, "state->next_iter in [0, iters]");
   SC4_ARG(state->next_iter > 0 || *held == nullptr, "a new run (next_iter = 0) holds no preconditioner");
   SC4_ARG(*held == nullptr || (*held)->n == P->n, "held preconditioner of another size");
+  SC4_ARG(*held == nullptr || o->sketch.method != SC4DVAR_SKETCH_NONE,
+          "a held preconditioner needs a sketch method (method NONE runs Prec_Gamma)");
   SC4_ARG(!o->line_search || (o->ls_c1 > 0 && o->ls_c1 < o->ls_c2 && o->ls_c2 < 1 && o->ls_alpha1 > 0),
           "line search constants: 0 < c1 < c2 < 1, alpha1 > 0");
   SC4_ARG(o->solve == 0 || (o->solve == 1 && o->sketch.method != SC4DVAR_SKETCH_NONE),
@@ -1813,6 +1815,13 @@ int sc4dvar_gauss_newton_resume(sc4dvar_problem_t P, const sc4dvar_gn_opts* o, d
   const int n = P->n;
   const int k0 = state->next_iter;
   if (info && k0 == 0) std::memset(info, 0, sizeof(*info));
+  if (info && k0 > 0) {
+    // the entries of this call start clean; those of earlier calls are kept
+    for (int i = k0; i < SC4DVAR_GN_MAX_ITERS; ++i) {
+      info->J[i] = info->g_inf[i] = info->relres[i] = info->kappa_re[i] = info->alpha[i] = 0.0;
+      info->pcg_its[i] = info->sketched[i] = info->rank[i] = info->ls_evals[i] = info->ls_status[i] = 0;
+    }
+  }
   Buf gb;
   SC4_TRY(gb.ensure((size_t)3 * n * sizeof(double)));
   double* g = gb.as<double>();

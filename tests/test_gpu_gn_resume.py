@@ -94,6 +94,8 @@ def test_resume_rejects_inconsistent_state():
     bad = g.GNCheckpoint(cp.v, 5, cp.g0_inf, cp.sketch_iter, cp.V, cp.lam, cp.counters, cp.record)
     with pytest.raises(g.Sc4dvarError):
         prob.gauss_newton_resume(v, 3, checkpoint=bad, **OPTS)        # next_iter beyond iters
+    with pytest.raises(g.Sc4dvarError):                                 # a held sketch with method none
+        prob.gauss_newton_resume(v, 3, checkpoint=cp, **dict(OPTS, method="none"))
     wrong_size = g.GNCheckpoint(np.zeros(wl.n + 1), 1, 1.0, -1, None, None, {}, [])
     with pytest.raises(ValueError):
         prob.gauss_newton_resume(v, 3, checkpoint=wrong_size, **OPTS)
