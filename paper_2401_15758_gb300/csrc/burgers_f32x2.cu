@@ -833,12 +833,14 @@ int cluster_for(int H, int k, int arrays) {
   int cl = 1;
   while ((size_t)(arrays * (H / cl + 2 * kPad2) + 256) * sizeof(f2) > kMaxSmem2 && cl < 16) cl *= 2;
   if (k <= 4) {
-    // few directions: spread each over up to 8 CTAs; SC4DVAR_FEW_CLUSTER caps
-    // the spread (a tuning knob: 1, 2, 4 or 8)
+    // few directions: SC4DVAR_FEW_CLUSTER (2, 4 or 8) spreads each over that
+    // many CTAs of a cluster. The default keeps one CTA per direction: the
+    // one-CTA sweeps beat the cluster sweeps, which wait on a cluster barrier per
+    // exchange (n = 8192, one direction: TLM + ADJ 79 ms on one SM, 101 ms on 8)
     static int cap = [] {
       const char* e = getenv("SC4DVAR_FEW_CLUSTER");
-      int c = e ? atoi(e) : 8;
-      return (c == 1 || c == 2 || c == 4) ? c : 8;
+      int c = e ? atoi(e) : 1;
+      return (c == 2 || c == 4 || c == 8) ? c : 1;
     }();
     while (cl < cap && H / (cl * 2) >= 256) cl *= 2;
   }

@@ -143,11 +143,12 @@ def test_errors_are_status_codes():
 V2_CASES = [
     # (n, output steps, k, precision)
     (8192, 20, 6, "fp32"),   # packed FP32x2, 8 pairs per thread, one CTA per direction
-    (8192, 20, 3, "fp32"),   # packed FP32x2 in an 8-CTA cluster (few directions)
+    (8192, 20, 3, "fp32"),   # packed FP32x2, few directions: one CTA each (the cluster form is
+                             # rerun under SC4DVAR_FEW_CLUSTER=8 by test_gpu_cluster_knob.py)
     (512, 20, 5, "fp32"),    # scalar register-resident kernels
     (8192, 20, 2, "fp64"),   # 16-CTA cluster, 512 points per CTA (few directions)
     (2048, 20, 5, "fp64"),   # 2 points per thread, odd k (FFT pair tail)
-    (1024, 20, 1, "fp32"),   # 2-CTA cluster
+    (1024, 20, 1, "fp32"),   # one direction, one CTA (a 2-CTA cluster under the knob)
 ]
 
 
