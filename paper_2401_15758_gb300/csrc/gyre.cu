@@ -383,51 +383,63 @@ struct TlmStage {
   bool last;
 };
 
+// Fields per thread of the stage kernels: the derivatives of the stored
+// trajectory (the same for every field) are formed once and reused, which cuts
+// the L1/L2 traffic of the neighbour loads that bound these kernels.
+constexpr int kGyFields = 4;
+
 template <typename T>
 __global__ void gy_tlm_stage_kernel(GyP<T> p, int k, const T* __restrict__ om_b, const T* __restrict__ ps_b,
                                     TlmStage<T> a) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = field
-  if (q >= p.n || (int)blockIdx.y >= k) return;
-  const int c = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = group of fields
+  const int c0 = (int)blockIdx.y * kGyFields;
+  if (q >= p.n || c0 >= k) return;
   const int j = q >> p.lnx, i = q & (p.nx - 1);
-  const size_t off = (size_t)c * p.n;
-  const T* X = a.dX + off;
-  const T* dp = a.dpsi + off;
-  const T Xc = X[q];
-  const T dxx = (at(X, i + 1, j, p) - at(X, i - 1, j, p)) * p.inv2h;
-  const T dxy = (at(X, i, j + 1, p) - at(X, i, j - 1, p)) * p.inv2h;
-  const T lap = (at(X, i + 1, j, p) + at(X, i - 1, j, p) + at(X, i, j + 1, p) + at(X, i, j - 1, p) -
-                 T(4) * Xc) * p.invh2;
-  const T dpx = (at(dp, i + 1, j, p) - at(dp, i - 1, j, p)) * p.inv2h;
-  const T dpy = (at(dp, i, j + 1, p) - at(dp, i, j - 1, p)) * p.inv2h;
   const T obx = (at(om_b, i + 1, j, p) - at(om_b, i - 1, j, p)) * p.inv2h;
   const T oby = (at(om_b, i, j + 1, p) - at(om_b, i, j - 1, p)) * p.inv2h;
   const T pbx = (at(ps_b, i + 1, j, p) - at(ps_b, i - 1, j, p)) * p.inv2h;
   const T pby = (at(ps_b, i, j + 1, p) - at(ps_b, i, j - 1, p)) * p.inv2h;
-  // -(J(dpsi, omega_b) + J(psi_b, dX)) + Ro^{-1} dpsi_x + Re^{-1} Lap dX
-  const T K = -((dpy * obx - dpx * oby) + (pby * dxx - pbx * dxy)) + p.ro_inv * dpx + p.re_inv * lap;
-  if (!a.last) a.K[a.s][off + q] = K;
-  T v = a.dom[off + q];
-  for (int jj = 0; jj < a.s; ++jj) v += a.cK[jj] * a.K[jj][off + q];
-  a.next[off + q] = v + a.cK[a.s] * K;
+#pragma unroll 1
+  for (int f = 0; f < kGyFields && c0 + f < k; ++f) {
+    const size_t off = (size_t)(c0 + f) * p.n;
+    const T* X = a.dX + off;
+    const T* dp = a.dpsi + off;
+    const T Xc = X[q];
+    const T dxx = (at(X, i + 1, j, p) - at(X, i - 1, j, p)) * p.inv2h;
+    const T dxy = (at(X, i, j + 1, p) - at(X, i, j - 1, p)) * p.inv2h;
+    const T lap = (at(X, i + 1, j, p) + at(X, i - 1, j, p) + at(X, i, j + 1, p) + at(X, i, j - 1, p) -
+                   T(4) * Xc) * p.invh2;
+    const T dpx = (at(dp, i + 1, j, p) - at(dp, i - 1, j, p)) * p.inv2h;
+    const T dpy = (at(dp, i, j + 1, p) - at(dp, i, j - 1, p)) * p.inv2h;
+    // -(J(dpsi, omega_b) + J(psi_b, dX)) + Ro^{-1} dpsi_x + Re^{-1} Lap dX
+    const T K = -((dpy * obx - dpx * oby) + (pby * dxx - pbx * dxy)) + p.ro_inv * dpx + p.re_inv * lap;
+    if (!a.last) a.K[a.s][off + q] = K;
+    T v = a.dom[off + q];
+    for (int jj = 0; jj < a.s; ++jj) v += a.cK[jj] * a.K[jj][off + q];
+    a.next[off + q] = v + a.cK[a.s] * K;
+  }
 }
 
 // ---------------------------------------------------------------- ADJ stage
 // first half: g = D_y(omega_b,x kappa) - D_x(omega_b,y kappa) - Ro^{-1} D_x kappa
 template <typename T>
 __global__ void gy_adj_pre_kernel(GyP<T> p, int k, const T* __restrict__ om_b, Comb<T> kap, T* __restrict__ gout) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = field
-  if (q >= p.n || (int)blockIdx.y >= k) return;
-  const int c = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = group of fields
+  const int c0 = (int)blockIdx.y * kGyFields;
+  if (q >= p.n || c0 >= k) return;
   const int j = q >> p.lnx, i = q & (p.nx - 1);
-  const size_t off = (size_t)c * p.n;
   auto obx = [&](int ii, int jj) { return (at(om_b, ii + 1, jj, p) - at(om_b, ii - 1, jj, p)) * p.inv2h; };
   auto oby = [&](int ii, int jj) { return (at(om_b, ii, jj + 1, p) - at(om_b, ii, jj - 1, p)) * p.inv2h; };
-  const T kE = comb_at(kap, off, i + 1, j, p), kW = comb_at(kap, off, i - 1, j, p);
-  const T kN = comb_at(kap, off, i, j + 1, p), kS = comb_at(kap, off, i, j - 1, p);
-  const T gy = (obx(i, j + 1) * kN - obx(i, j - 1) * kS) * p.inv2h;
-  const T gx = (oby(i + 1, j) * kE - oby(i - 1, j) * kW) * p.inv2h;
-  gout[off + q] = gy - gx - p.ro_inv * (kE - kW) * p.inv2h;
+  const T obxN = obx(i, j + 1), obxS = obx(i, j - 1), obyE = oby(i + 1, j), obyW = oby(i - 1, j);
+#pragma unroll 1
+  for (int f = 0; f < kGyFields && c0 + f < k; ++f) {
+    const size_t off = (size_t)(c0 + f) * p.n;
+    const T kE = comb_at(kap, off, i + 1, j, p), kW = comb_at(kap, off, i - 1, j, p);
+    const T kN = comb_at(kap, off, i, j + 1, p), kS = comb_at(kap, off, i, j - 1, p);
+    const T gy = (obxN * kN - obxS * kS) * p.inv2h;
+    const T gx = (obyE * kE - obyW * kW) * p.inv2h;
+    gout[off + q] = gy - gx - p.ro_inv * (kE - kW) * p.inv2h;
+  }
 }
 
 template <typename T>
@@ -443,26 +455,30 @@ struct AdjPost {
 template <typename T>
 __global__ void gy_adj_post_kernel(GyP<T> p, int k, const T* __restrict__ ps_b, Comb<T> kap, AdjPost<T> a,
                                    int S) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = field
-  if (q >= p.n || (int)blockIdx.y >= k) return;
-  const int c = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // grid point; blockIdx.y = group of fields
+  const int c0 = (int)blockIdx.y * kGyFields;
+  if (q >= p.n || c0 >= k) return;
   const int j = q >> p.lnx, i = q & (p.nx - 1);
-  const size_t off = (size_t)c * p.n;
   auto pbx = [&](int ii, int jj) { return (at(ps_b, ii + 1, jj, p) - at(ps_b, ii - 1, jj, p)) * p.inv2h; };
   auto pby = [&](int ii, int jj) { return (at(ps_b, ii, jj + 1, p) - at(ps_b, ii, jj - 1, p)) * p.inv2h; };
-  const T kC = comb_at(kap, off, i, j, p);
-  const T kE = comb_at(kap, off, i + 1, j, p), kW = comb_at(kap, off, i - 1, j, p);
-  const T kN = comb_at(kap, off, i, j + 1, p), kS = comb_at(kap, off, i, j - 1, p);
-  const T tx = (pby(i + 1, j) * kE - pby(i - 1, j) * kW) * p.inv2h;
-  const T ty = (pbx(i, j + 1) * kN - pbx(i, j - 1) * kS) * p.inv2h;
-  const T lap = (kE + kW + kN + kS - T(4) * kC) * p.invh2;
-  const T th = tx - ty + p.re_inv * lap + a.phi[off + q];
-  if (a.s > 0) {
-    a.Th[a.s][off + q] = th;
-  } else {
-    T v = a.lam[off + q] + th;
-    for (int jj = 1; jj < S; ++jj) v += a.Th[jj][off + q];
-    a.lam_out[off + q] = v;
+  const T pbyE = pby(i + 1, j), pbyW = pby(i - 1, j), pbxN = pbx(i, j + 1), pbxS = pbx(i, j - 1);
+#pragma unroll 1
+  for (int f = 0; f < kGyFields && c0 + f < k; ++f) {
+    const size_t off = (size_t)(c0 + f) * p.n;
+    const T kC = comb_at(kap, off, i, j, p);
+    const T kE = comb_at(kap, off, i + 1, j, p), kW = comb_at(kap, off, i - 1, j, p);
+    const T kN = comb_at(kap, off, i, j + 1, p), kS = comb_at(kap, off, i, j - 1, p);
+    const T tx = (pbyE * kE - pbyW * kW) * p.inv2h;
+    const T ty = (pbxN * kN - pbxS * kS) * p.inv2h;
+    const T lap = (kE + kW + kN + kS - T(4) * kC) * p.invh2;
+    const T th = tx - ty + p.re_inv * lap + a.phi[off + q];
+    if (a.s > 0) {
+      a.Th[a.s][off + q] = th;
+    } else {
+      T v = a.lam[off + q] + th;
+      for (int jj = 1; jj < S; ++jj) v += a.Th[jj][off + q];
+      a.lam_out[off + q] = v;
+    }
   }
 }
 
@@ -684,7 +700,7 @@ int gyre_tlm(const GyreGeom& g, const T* U0, int ldu, int k, T* W, int ldw, void
       }
       a.s = s;
       const size_t row = ((size_t)t * g.S + s) * n;
-      gy_tlm_stage_kernel<T><<<dim3(blocks_of(n), k), 256, 0, st>>>(p, k, om + row, ps + row, a);
+      gy_tlm_stage_kernel<T><<<dim3(blocks_of(n), div_up(k, kGyFields)), 256, 0, st>>>(p, k, om + row, ps + row, a);
       SC4_LAUNCH_CHECK();
     }
     const int oi = g.obs_of_step_h[t + 1];
@@ -741,7 +757,7 @@ int gyre_adj(const GyreGeom& g, const T* W, int ldw, int k, T* Out, int ldo, voi
         kap.c[q] = T(0);
       }
       const size_t row = ((size_t)(t - 1) * g.S + s) * n;
-      gy_adj_pre_kernel<T><<<dim3(blocks_of(n), k), 256, 0, st>>>(p, k, om + row, kap, gb);
+      gy_adj_pre_kernel<T><<<dim3(blocks_of(n), div_up(k, kGyFields)), 256, 0, st>>>(p, k, om + row, kap, gb);
       SC4_LAUNCH_CHECK();
       SC4_TRY(poisson<T>(g, k, gb, phi, tmp, st));
       AdjPost<T> a{};
@@ -750,7 +766,7 @@ int gyre_adj(const GyreGeom& g, const T* W, int ldw, int k, T* Out, int ldo, voi
       a.lam_out = lam[cur ^ 1];
       for (int q = 0; q < 4; ++q) a.Th[q] = Th[q];
       a.s = s;
-      gy_adj_post_kernel<T><<<dim3(blocks_of(n), k), 256, 0, st>>>(p, k, ps + row, kap, a, g.S);
+      gy_adj_post_kernel<T><<<dim3(blocks_of(n), div_up(k, kGyFields)), 256, 0, st>>>(p, k, ps + row, kap, a, g.S);
       SC4_LAUNCH_CHECK();
     }
     cur ^= 1;
